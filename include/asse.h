@@ -1,0 +1,218 @@
+/*
+ * asse.h -- C ABI of the GB300 (sm_103a) ASSE library: sliding-window
+ * super-point detection and cardinality estimation with asynchronous
+ * timestamps (Xu, arXiv 1807.01527).
+ *
+ * One pool (an "ATV cube": r rows x 2^(c+u) ATVs x g ATs, Sec. 4) lives in
+ * device memory owned by the library.  A slice is processed as
+ *
+ *     asse_ingest(...)       any number of batches of (aip, bip) pairs
+ *     asse_close_slice(...)  scan + refresh + restore + estimate, then the
+ *                            next slice opens
+ *     asse_report(...)       read the super points of the window just closed
+ *
+ * or, step by step, asse_scan -> asse_restore -> [asse_estimate] ->
+ * asse_advance (identical results; close_slice fuses the refresh into the
+ * scan).
+ *
+ * Conventions for every entry point:
+ *  - Return value: ASSE_OK (0) or one of the ASSE_E* codes; no exception or
+ *    device trap ever crosses the ABI.  asse_last_error() returns a message
+ *    for the last failing call on a pool.
+ *  - Pointers are plain host or device addresses; `where` says which
+ *    (ASSE_HOST / ASSE_DEVICE).  The caller owns every buffer it passes.
+ *  - All work is enqueued on the pool's CUDA stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and is asynchronous unless the
+ *    entry point says it synchronises.
+ *  - A pool is not thread-safe; distinct pools may be used from distinct
+ *    threads and streams.
+ */
+#ifndef ASSE_H
+#define ASSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define ASSE_OK 0
+#define ASSE_EINVAL 1    /* invalid argument or parameter combination */
+#define ASSE_ENOMEM 2    /* device or host allocation failed */
+#define ASSE_ECAPACITY 3 /* an output or the restore scratch is too small */
+#define ASSE_ECUDA 4     /* a CUDA runtime call or kernel launch failed */
+#define ASSE_ESTATE 5    /* call out of order (e.g. restore before scan) */
+
+/* Buffer locations. */
+#define ASSE_HOST 0
+#define ASSE_DEVICE 1
+
+/* Counter kinds. */
+#define ASSE_COUNTER_AT 0  /* asynchronous timestamp, log2(2k+1) bits (Sec. 3) */
+#define ASSE_COUNTER_ACE 1 /* aging counter, log2(k+1) bits, decremented every slice (Sec. 2.3) */
+
+/* Flags of asse_superpoint. */
+#define ASSE_SP_SATURATED 1u /* NAT == g: Eq. 4 is +infinity */
+#define ASSE_SP_REPORTED 2u  /* estimate >= theta */
+
+/* Pool parameters (Sec. 3 and Sec. 4.1).
+ *  k       window size in slices (1..127); AT values are 0..2k, 2k inactive.
+ *  theta   super-point threshold on the cardinality (Sec. 2.1).
+ *  g       ATs per ATV, 2k <= g <= 65535.  The 2k ACT blocks are contiguous:
+ *          the first 2k-1 hold floor(g/2k) ATs each, the last the rest.
+ *  r       rows, 2..8.
+ *  c       column-index bits (ATVs per row and frame = 2^c), 1..16.
+ *  u       frame bits (frames = 2^u), 0..8; c + u <= 24.
+ *  s       offset between consecutive rows' column windows on LBS(f, 32-u):
+ *          1 <= s <= c, s*(r-1) < 32-u, and c + s*(r-1) >= 32-u
+ *          (completeness, Sec. 4.1).
+ *  A       mangling multiplier of f(aip) = A*aip mod (2^32+15), 2 <= A < 2^32.
+ *  bh_a    BH multiplier (must be odd), bh_b BH offset:
+ *          BH(bip) = (hi32(bh_a*bip + bh_b mod 2^64) * g) >> 32.
+ *  counter ASSE_COUNTER_AT or ASSE_COUNTER_ACE.
+ *  restore_cap  column tuples held per frame at any join level of the
+ *          restore; 0 selects 4096.  The candidate lists hold up to
+ *          restore_cap * 2^u entries.
+ *  max_batch    device staging capacity in pairs for ASSE_HOST ingest
+ *          (copied in chunks of this size); 0 selects 4 Mi.
+ */
+typedef struct asse_config {
+    uint32_t k, theta, g, r, c, u, s, A;
+    uint64_t bh_a, bh_b;
+    uint32_t counter;
+    uint32_t restore_cap;
+    uint64_t max_batch;
+} asse_config;
+
+/* One candidate or reported super point (Sec. 4.2-4.3). */
+typedef struct asse_superpoint {
+    uint32_t aip;   /* restored host address */
+    uint32_t nat;   /* NAT(aip), Algorithm 5 */
+    float est;      /* Eq. 4 estimate (evaluated in FP64, stored FP32); +inf if saturated */
+    uint32_t flags; /* ASSE_SP_* */
+} asse_superpoint;
+
+/* Derived layout of a pool, for callers that read the packed state. */
+typedef struct asse_pool_info {
+    uint32_t w;          /* bits per counter: ceil(log2(2k+1)) (AT) or ceil(log2(k+1)) (ACE) */
+    uint32_t fields;     /* counters per 32-bit word: floor(32/w); field j at bits [j*w, j*w+w) */
+    uint32_t words;      /* 32-bit words per ATV, ceil(g/fields) rounded up to a multiple of 8 */
+    uint32_t E;          /* ATVs per row: 2^(c+u); ATV index in a row = (frame << c) | column */
+    uint32_t threshold;  /* super-ATV count threshold ceil(g - g*exp(-theta/g)) (Sec. 4.2) */
+    uint32_t block;      /* ATs per ACT block: floor(g/2k) */
+    uint64_t slice;      /* index of the open slice (0 after create) */
+    uint64_t pool_words; /* r * E * words */
+    const uint32_t *pool;/* device address of the packed pool, [r][E][words] */
+} asse_pool_info;
+
+typedef struct asse_pool asse_pool;
+
+/* Create a pool: validate cfg, allocate the device state, InitAT every
+ * counter (Sec. 3: value 2k; ACE: 0), open slice 0.  stream is the
+ * cudaStream_t all later work of this pool is enqueued on.  Synchronises.
+ * Errors: EINVAL (cfg), ENOMEM, ECUDA.  *out is NULL on error. */
+int asse_create(const asse_config *cfg, void *stream, asse_pool **out);
+
+/* Free every device and host resource of the pool (NULL is ignored).
+ * Synchronises the pool's stream first. */
+void asse_destroy(asse_pool *pool);
+
+/* Change the stream later work is enqueued on. */
+int asse_set_stream(asse_pool *pool, void *stream);
+
+/* Algorithm 3 (Scan IP pair, Sec. 4.1) on n pairs of the open slice.
+ * pairs: n (aip, bip) uint32 pairs, interleaved (aip0, bip0, aip1, ...).
+ *   ASSE_DEVICE: a device address, 16-byte aligned, that must stay valid
+ *   until the stream reaches this work; nothing is copied.
+ *   ASSE_HOST: host memory (pinned for overlap); copied in max_batch chunks
+ *   into device staging, the copy of chunk i+1 overlapping the ingest of
+ *   chunk i; the host buffer may be reused when the call returns.
+ * Order and repetition of pairs within a slice do not change the result.
+ * Errors: EINVAL (NULL with n > 0, misalignment), ECUDA. */
+int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);
+
+/* Close the open slice for the window of the latest kp slices (1 <= kp <= k):
+ * the per-ATV active counts |ATV|^{k'} (Algorithm 1, Sec. 3), the row-frame
+ * loads |AAT(k',i,j)| (Sec. 4.3), the super ATVs SA(i,j) (Sec. 4.2), with
+ * preserveAT (Algorithm 2) for the next slice fused into the same pass; then
+ * the restore (Algorithm 4) and, for every candidate, NAT (Algorithm 5) and
+ * Eq. 4; then slice t+1 opens.  Asynchronous.  A restore that needs more
+ * than restore_cap tuples is reported by asse_report / asse_candidates.
+ * Errors: EINVAL (kp), ECUDA. */
+int asse_close_slice(asse_pool *pool, uint32_t kp);
+
+/* Stepwise close, part 1: the scan of asse_close_slice without the refresh.
+ * The pool state is unchanged.  Asynchronous.  Errors: EINVAL, ECUDA. */
+int asse_scan(asse_pool *pool, uint32_t kp);
+
+/* Stepwise close, part 2: Algorithm 4, Algorithm 5 and Eq. 4 on the super
+ * ATVs of the last scan.  Asynchronous.  Errors: ESTATE (no scan), ECUDA. */
+int asse_restore(asse_pool *pool);
+
+/* Stepwise close, part 3: preserveAT (Algorithm 2) on the two ACT blocks of
+ * every ATV whose ACT becomes 0 or k in the next slice (AT pool), or the
+ * per-slice decrement of every aging counter (ACE pool); then the next
+ * slice opens.  Asynchronous.  Errors: ECUDA. */
+int asse_advance(asse_pool *pool);
+
+/* Sec. 4.3 for arbitrary hosts: NAT (Algorithm 5) and Eq. 4 of each of the
+ * n addresses in aips, for the window and loads of the last scan.  Must run
+ * after asse_scan and before asse_advance (the refresh changes the state).
+ * aips and out live at `where` (both host or both device); out[i].flags has
+ * ASSE_SP_REPORTED when est >= theta.  Host buffers synchronise.
+ * Errors: ESTATE, EINVAL, ECUDA. */
+int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, asse_superpoint *out, int where);
+
+/* Read the super points reported by the last close/restore: the candidates
+ * whose Eq. 4 estimate is >= theta, in unspecified order.  Copies
+ * min(count, cap) entries to out (host or device), stores the count in
+ * *n_out, and synchronises the stream.  Returns ECAPACITY if cap < count, or
+ * if the restore overflowed restore_cap (then *n_out is the number of
+ * column tuples the overflowing join level needed, a lower bound on the
+ * capacity to configure, and out is not written).  Errors: ESTATE, ECUDA. */
+int asse_report(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
+
+/* As asse_report, but every restored candidate (CSIP, Algorithm 4), reported
+ * or not. */
+int asse_candidates(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
+
+/* Per-ATV active counts of the last scan, r*E uint16 ([row][ATV]), copied to
+ * out at `where`.  Host copies synchronise.  Errors: ESTATE, ECUDA. */
+int asse_counts(asse_pool *pool, uint16_t *out, int where);
+
+/* Row-frame loads |AAT(k',i,j)| of the last scan, r*2^u uint64 ([row][frame]),
+ * copied to host memory.  Synchronises.  Errors: ESTATE, ECUDA. */
+int asse_loads(asse_pool *pool, uint64_t *out);
+
+/* Layout of the packed pool and the open slice index. */
+int asse_pool_info(const asse_pool *pool, asse_pool_info *out);
+
+/* Copy the packed pool (pool_words uint32) to out at `where`.  Host copies
+ * synchronise.  Errors: ECUDA. */
+int asse_read_pool(asse_pool *pool, uint32_t *out, int where);
+
+/* Checkpoint: write a self-describing image of the pool (header with cfg and
+ * slice index, then the packed words) to host memory dst of cap bytes.
+ * *n_out receives the image size; with dst == NULL only the size is
+ * returned.  Synchronises.  Errors: ECAPACITY (cap too small), ECUDA. */
+int asse_snapshot(asse_pool *pool, void *dst, uint64_t cap, uint64_t *n_out);
+
+/* Restore a pool from an image written by asse_snapshot of a pool with the
+ * same cfg (checked).  Synchronises.  Errors: EINVAL (mismatch), ECUDA. */
+int asse_load(asse_pool *pool, const void *src, uint64_t n);
+
+/* Number of kernels this pool has launched since creation. */
+uint64_t asse_launches(const asse_pool *pool);
+
+/* Message of the last failing call on pool ("" if none). */
+const char *asse_last_error(const asse_pool *pool);
+
+/* Name of a status code. */
+const char *asse_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASSE_H */
