@@ -37,6 +37,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define ASSE_API __attribute__((visibility("default")))
+#else
+#define ASSE_API
+#endif
+
 /* Status codes. */
 #define ASSE_OK 0
 #define ASSE_EINVAL 1    /* invalid argument or parameter combination */
@@ -113,14 +119,14 @@ typedef struct asse_pool asse_pool;
  * counter (Sec. 3: value 2k; ACE: 0), open slice 0.  stream is the
  * cudaStream_t all later work of this pool is enqueued on.  Synchronises.
  * Errors: EINVAL (cfg), ENOMEM, ECUDA.  *out is NULL on error. */
-int asse_create(const asse_config *cfg, void *stream, asse_pool **out);
+ASSE_API int asse_create(const asse_config *cfg, void *stream, asse_pool **out);
 
 /* Free every device and host resource of the pool (NULL is ignored).
  * Synchronises the pool's stream first. */
-void asse_destroy(asse_pool *pool);
+ASSE_API void asse_destroy(asse_pool *pool);
 
 /* Change the stream later work is enqueued on. */
-int asse_set_stream(asse_pool *pool, void *stream);
+ASSE_API int asse_set_stream(asse_pool *pool, void *stream);
 
 /* Algorithm 3 (Scan IP pair, Sec. 4.1) on n pairs of the open slice.
  * pairs: n (aip, bip) uint32 pairs, interleaved (aip0, bip0, aip1, ...).
@@ -131,7 +137,7 @@ int asse_set_stream(asse_pool *pool, void *stream);
  *   chunk i; the host buffer may be reused when the call returns.
  * Order and repetition of pairs within a slice do not change the result.
  * Errors: EINVAL (NULL with n > 0, misalignment), ECUDA. */
-int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);
+ASSE_API int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);
 
 /* Close the open slice for the window of the latest kp slices (1 <= kp <= k):
  * the per-ATV active counts |ATV|^{k'} (Algorithm 1, Sec. 3), the row-frame
@@ -141,21 +147,21 @@ int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);
  * Eq. 4; then slice t+1 opens.  Asynchronous.  A restore that needs more
  * than restore_cap tuples is reported by asse_report / asse_candidates.
  * Errors: EINVAL (kp), ECUDA. */
-int asse_close_slice(asse_pool *pool, uint32_t kp);
+ASSE_API int asse_close_slice(asse_pool *pool, uint32_t kp);
 
 /* Stepwise close, part 1: the scan of asse_close_slice without the refresh.
  * The pool state is unchanged.  Asynchronous.  Errors: EINVAL, ECUDA. */
-int asse_scan(asse_pool *pool, uint32_t kp);
+ASSE_API int asse_scan(asse_pool *pool, uint32_t kp);
 
 /* Stepwise close, part 2: Algorithm 4, Algorithm 5 and Eq. 4 on the super
  * ATVs of the last scan.  Asynchronous.  Errors: ESTATE (no scan), ECUDA. */
-int asse_restore(asse_pool *pool);
+ASSE_API int asse_restore(asse_pool *pool);
 
 /* Stepwise close, part 3: preserveAT (Algorithm 2) on the two ACT blocks of
  * every ATV whose ACT becomes 0 or k in the next slice (AT pool), or the
  * per-slice decrement of every aging counter (ACE pool); then the next
  * slice opens.  Asynchronous.  Errors: ECUDA. */
-int asse_advance(asse_pool *pool);
+ASSE_API int asse_advance(asse_pool *pool);
 
 /* Sec. 4.3 for arbitrary hosts: NAT (Algorithm 5) and Eq. 4 of each of the
  * n addresses in aips, for the window and loads of the last scan.  Must run
@@ -163,7 +169,7 @@ int asse_advance(asse_pool *pool);
  * aips and out live at `where` (both host or both device); out[i].flags has
  * ASSE_SP_REPORTED when est >= theta.  Host buffers synchronise.
  * Errors: ESTATE, EINVAL, ECUDA. */
-int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, asse_superpoint *out, int where);
+ASSE_API int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, asse_superpoint *out, int where);
 
 /* Read the super points reported by the last close/restore: the candidates
  * whose Eq. 4 estimate is >= theta, in unspecified order.  Copies
@@ -172,45 +178,45 @@ int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, asse_superp
  * if the restore overflowed restore_cap (then *n_out is the number of
  * column tuples the overflowing join level needed, a lower bound on the
  * capacity to configure, and out is not written).  Errors: ESTATE, ECUDA. */
-int asse_report(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
+ASSE_API int asse_report(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
 
 /* As asse_report, but every restored candidate (CSIP, Algorithm 4), reported
  * or not. */
-int asse_candidates(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
+ASSE_API int asse_candidates(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
 
 /* Per-ATV active counts of the last scan, r*E uint16 ([row][ATV]), copied to
  * out at `where`.  Host copies synchronise.  Errors: ESTATE, ECUDA. */
-int asse_counts(asse_pool *pool, uint16_t *out, int where);
+ASSE_API int asse_counts(asse_pool *pool, uint16_t *out, int where);
 
 /* Row-frame loads |AAT(k',i,j)| of the last scan, r*2^u uint64 ([row][frame]),
  * copied to host memory.  Synchronises.  Errors: ESTATE, ECUDA. */
-int asse_loads(asse_pool *pool, uint64_t *out);
+ASSE_API int asse_loads(asse_pool *pool, uint64_t *out);
 
 /* Layout of the packed pool and the open slice index. */
-int asse_pool_info(const asse_pool *pool, asse_pool_info *out);
+ASSE_API int asse_info(const asse_pool *pool, asse_pool_info *out);
 
 /* Copy the packed pool (pool_words uint32) to out at `where`.  Host copies
  * synchronise.  Errors: ECUDA. */
-int asse_read_pool(asse_pool *pool, uint32_t *out, int where);
+ASSE_API int asse_read_pool(asse_pool *pool, uint32_t *out, int where);
 
 /* Checkpoint: write a self-describing image of the pool (header with cfg and
  * slice index, then the packed words) to host memory dst of cap bytes.
  * *n_out receives the image size; with dst == NULL only the size is
  * returned.  Synchronises.  Errors: ECAPACITY (cap too small), ECUDA. */
-int asse_snapshot(asse_pool *pool, void *dst, uint64_t cap, uint64_t *n_out);
+ASSE_API int asse_snapshot(asse_pool *pool, void *dst, uint64_t cap, uint64_t *n_out);
 
 /* Restore a pool from an image written by asse_snapshot of a pool with the
  * same cfg (checked).  Synchronises.  Errors: EINVAL (mismatch), ECUDA. */
-int asse_load(asse_pool *pool, const void *src, uint64_t n);
+ASSE_API int asse_load(asse_pool *pool, const void *src, uint64_t n);
 
 /* Number of kernels this pool has launched since creation. */
-uint64_t asse_launches(const asse_pool *pool);
+ASSE_API uint64_t asse_launches(const asse_pool *pool);
 
 /* Message of the last failing call on pool ("" if none). */
-const char *asse_last_error(const asse_pool *pool);
+ASSE_API const char *asse_last_error(const asse_pool *pool);
 
 /* Name of a status code. */
-const char *asse_strerror(int status);
+ASSE_API const char *asse_strerror(int status);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,250 @@
+"""ctypes binding of libasse.so (include/asse.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+passes pointers, sizes and the current torch CUDA stream, and turns status
+codes into exceptions.  There is no fallback: if the library is not built,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libasse.so")
+
+OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE = 0, 1, 2, 3, 4, 5
+HOST, DEVICE = 0, 1
+COUNTER_AT, COUNTER_ACE = 0, 1
+SP_SATURATED, SP_REPORTED = 1, 2
+
+u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("k", u32), ("theta", u32), ("g", u32), ("r", u32), ("c", u32), ("u", u32), ("s", u32),
+                ("A", u32), ("bh_a", u64), ("bh_b", u64), ("counter", u32), ("restore_cap", u32),
+                ("max_batch", u64)]
+
+
+class SuperPoint(ctypes.Structure):
+    _fields_ = [("aip", u32), ("nat", u32), ("est", ctypes.c_float), ("flags", u32)]
+
+
+class PoolInfo(ctypes.Structure):
+    _fields_ = [("w", u32), ("fields", u32), ("words", u32), ("E", u32), ("threshold", u32), ("block", u32),
+                ("slice", u64), ("pool_words", u64), ("pool", vp)]
+
+
+SP_DTYPE = np.dtype([("aip", "<u4"), ("nat", "<u4"), ("est", "<f4"), ("flags", "<u4")])
+
+# Every entry point of include/asse.h: name -> (restype, argtypes).
+EXPORTS = {
+    "asse_create": (i32, [ctypes.POINTER(Config), vp, ctypes.POINTER(vp)]),
+    "asse_destroy": (None, [vp]),
+    "asse_set_stream": (i32, [vp, vp]),
+    "asse_ingest": (i32, [vp, vp, u64, i32]),
+    "asse_close_slice": (i32, [vp, u32]),
+    "asse_scan": (i32, [vp, u32]),
+    "asse_restore": (i32, [vp]),
+    "asse_advance": (i32, [vp]),
+    "asse_estimate": (i32, [vp, vp, u64, vp, i32]),
+    "asse_report": (i32, [vp, vp, u64, ctypes.POINTER(u64), i32]),
+    "asse_candidates": (i32, [vp, vp, u64, ctypes.POINTER(u64), i32]),
+    "asse_counts": (i32, [vp, vp, i32]),
+    "asse_loads": (i32, [vp, vp]),
+    "asse_info": (i32, [vp, ctypes.POINTER(PoolInfo)]),
+    "asse_read_pool": (i32, [vp, vp, i32]),
+    "asse_snapshot": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
+    "asse_load": (i32, [vp, vp, u64]),
+    "asse_launches": (u64, [vp]),
+    "asse_last_error": (ctypes.c_char_p, [vp]),
+    "asse_strerror": (ctypes.c_char_p, [i32]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libasse.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libasse.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class AsseError(RuntimeError):
+    def __init__(self, status: int, message: str, n_needed: int | None = None):
+        super().__init__("%s: %s" % (lib().asse_strerror(status).decode(), message))
+        self.status = status
+        self.n_needed = n_needed
+
+
+def _current_stream() -> int:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _pairs_arg(pairs):
+    """(pointer, n, where, keepalive) of an (n, 2) 32-bit pair array."""
+    if _is_torch(pairs):
+        if pairs.element_size() != 4 or not pairs.is_contiguous():
+            raise ValueError("pairs must be a contiguous 32-bit tensor")
+        n = pairs.numel() // 2
+        return pairs.data_ptr(), n, DEVICE if pairs.is_cuda else HOST, pairs
+    a = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1)
+    return a.ctypes.data, a.size // 2, HOST, a
+
+
+def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
+    """Packed pool words [r][E][words] -> counter values [r][E][g] (uint8):
+    field j of a word holds bits [j*w, j*w+w), AT h lives in word h // fields."""
+    w, F = info["w"], info["fields"]
+    words = words.reshape(-1, info["E"], info["words"])
+    h = np.arange(g)
+    sel = words[:, :, h // F]
+    return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
+
+
+class Pool:
+    """One ATV cube in device memory (include/asse.h)."""
+
+    def __init__(self, params: dict, *, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
+                 stream: int | None = None):
+        cfg = Config(int(params["k"]), int(params["theta"]), int(params["g"]), int(params["r"]), int(params["c"]),
+                     int(params["u"]), int(params["s"]), int(params["A"]), int(params["bh_a"]),
+                     int(params["bh_b"]), COUNTER_ACE if counter == "ace" else COUNTER_AT, int(restore_cap),
+                     int(max_batch))
+        self.cfg = cfg
+        self._h = vp()
+        self._stream = _current_stream() if stream is None else stream
+        rc = lib().asse_create(ctypes.byref(cfg), vp(self._stream), ctypes.byref(self._h))
+        if rc != OK:
+            raise AsseError(rc, lib().asse_last_error(None).decode())
+        self.r, self.g, self.k = cfg.r, cfg.g, cfg.k
+        self.frames = 1 << cfg.u
+        self.cap = restore_cap or 4096
+        self.out_cap = self.cap * self.frames
+        self._info = self.info()
+
+    # -- plumbing
+    def _check(self, rc: int, n_needed=None):
+        if rc != OK:
+            raise AsseError(rc, lib().asse_last_error(self._h).decode(), n_needed)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().asse_destroy(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: int):
+        self._stream = stream
+        self._check(lib().asse_set_stream(self._h, vp(stream)))
+
+    @property
+    def launches(self) -> int:
+        return int(lib().asse_launches(self._h))
+
+    def info(self) -> dict:
+        inf = PoolInfo()
+        self._check(lib().asse_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in PoolInfo._fields_}
+
+    # -- slice lifecycle
+    def ingest(self, pairs):
+        ptr, n, where, _keep = _pairs_arg(pairs)
+        self._check(lib().asse_ingest(self._h, vp(ptr), n, where))
+
+    def close_slice(self, kp: int | None = None):
+        self._check(lib().asse_close_slice(self._h, self.k if kp is None else kp))
+
+    def scan(self, kp: int | None = None):
+        self._check(lib().asse_scan(self._h, self.k if kp is None else kp))
+
+    def restore(self):
+        self._check(lib().asse_restore(self._h))
+
+    def advance(self):
+        self._check(lib().asse_advance(self._h))
+
+    # -- results
+    def _list(self, fn, out=None):
+        n = u64(0)
+        if out is not None:       # device tensor of SuperPoint records
+            rc = fn(self._h, vp(out.data_ptr()), out.numel() * out.element_size() // 16, ctypes.byref(n), DEVICE)
+            self._check(rc, int(n.value))
+            return int(n.value)
+        buf = np.zeros(self.out_cap, dtype=SP_DTYPE)
+        rc = fn(self._h, vp(buf.ctypes.data), self.out_cap, ctypes.byref(n), HOST)
+        self._check(rc, int(n.value))
+        return buf[: int(n.value)]
+
+    def report(self, out=None):
+        """Reported super points of the last close (structured array)."""
+        return self._list(lib().asse_report, out)
+
+    def candidates(self, out=None):
+        """Every restored candidate (CSIP) of the last close."""
+        return self._list(lib().asse_candidates, out)
+
+    def estimate(self, aips):
+        """NAT and Eq. 4 of given hosts, between scan() and advance()."""
+        if _is_torch(aips):
+            import torch
+            out = torch.zeros(aips.numel() * 4, dtype=torch.int32, device=aips.device)
+            self._check(lib().asse_estimate(self._h, vp(aips.data_ptr()), aips.numel(), vp(out.data_ptr()),
+                                            DEVICE))
+            return out
+        a = np.ascontiguousarray(aips, dtype=np.uint32)
+        out = np.zeros(a.size, dtype=SP_DTYPE)
+        self._check(lib().asse_estimate(self._h, vp(a.ctypes.data), a.size, vp(out.ctypes.data), HOST))
+        return out
+
+    def counts(self) -> np.ndarray:
+        out = np.zeros((self.r, self._info["E"]), dtype=np.uint16)
+        self._check(lib().asse_counts(self._h, vp(out.ctypes.data), HOST))
+        return out
+
+    def loads(self) -> np.ndarray:
+        out = np.zeros((self.r, self.frames), dtype=np.uint64)
+        self._check(lib().asse_loads(self._h, vp(out.ctypes.data)))
+        return out
+
+    def read_pool(self) -> np.ndarray:
+        inf = self._info
+        out = np.zeros(inf["pool_words"], dtype=np.uint32)
+        self._check(lib().asse_read_pool(self._h, vp(out.ctypes.data), HOST))
+        return out.reshape(self.r, inf["E"], inf["words"])
+
+    def state(self) -> np.ndarray:
+        """Counter values [r][E][g] decoded from the packed pool."""
+        return unpack_pool(self.read_pool(), self._info, self.g)
+
+    def snapshot(self) -> bytes:
+        n = u64(0)
+        self._check(lib().asse_snapshot(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(lib().asse_snapshot(self._h, buf, n.value, ctypes.byref(n)))
+        return buf.raw
+
+    def load(self, image: bytes):
+        self._check(lib().asse_load(self._h, image, len(image)))

@@ -1,0 +1,688 @@
+// Host side of the ASSE C ABI (include/asse.h): parameter validation, device
+// state, the slice lifecycle and the copies across the process/device
+// boundary.  All device work goes through the launchers of asse_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "asse_internal.h"
+
+using namespace asse;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct SnapHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    asse_config cfg;
+    uint64_t slice;
+    uint64_t pool_words;
+    uint32_t w, words;
+};
+
+}  // namespace
+
+struct asse_pool {
+    asse_config cfg{};
+    Params P{};
+    uint32_t w = 0, F = 0, words_used = 0, blk = 0;
+    uint64_t t = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    int sms = 0;
+    uint32_t *pool = nullptr;
+    uint64_t pool_words = 0;
+    uint16_t *cnt = nullptr;
+    unsigned long long *aat = nullptr;
+    uint32_t *sa_n = nullptr, *sa_x = nullptr, *sa_mask = nullptr;
+    Tuple *scratch = nullptr;
+    uint32_t cap = 0;
+    asse_superpoint *csip = nullptr, *report = nullptr;
+    uint64_t out_cap = 0;
+    Status *status = nullptr;
+    Status *status_host = nullptr;
+    uint32_t *stage[2] = {nullptr, nullptr};
+    uint64_t stage_pairs = 0;
+    uint32_t *q_aips = nullptr;
+    asse_superpoint *q_out = nullptr;
+    uint64_t q_cap = 0;
+    int scanned = 0, refreshed = 0, restored = 0, ingested = 0;
+    uint32_t scan_kp = 0;
+    uint64_t scan_slice = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(asse_pool *p, int code, const std::string &msg)
+{
+    if (p)
+        p->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(asse_pool *p, cudaError_t e, const char *what)
+{
+    return fail(p, ASSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(p, call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess)                        \
+            return cuda_fail((p), e_, #call);         \
+    } while (0)
+
+uint32_t ceil_log2(uint32_t v)
+{
+    uint32_t b = 0;
+    while ((1u << b) < v)
+        b++;
+    return b;
+}
+
+uint64_t inverse_mod(uint64_t a, uint64_t m)
+{
+    __int128 t0 = 0, t1 = 1, r0 = (__int128)m, r1 = (__int128)a;
+    while (r1 != 0) {
+        __int128 q = r0 / r1, tmp;
+        tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+        tmp = t0 - q * t1; t0 = t1; t1 = tmp;
+    }
+    if (t0 < 0)
+        t0 += (__int128)m;
+    return (uint64_t)t0;
+}
+
+int validate(const asse_config *c, std::string &why)
+{
+    char buf[256];
+    auto bad = [&](const char *m) { why = m; return ASSE_EINVAL; };
+    if (!c)
+        return bad("cfg is NULL");
+    if (c->counter != ASSE_COUNTER_AT && c->counter != ASSE_COUNTER_ACE)
+        return bad("counter must be ASSE_COUNTER_AT or ASSE_COUNTER_ACE");
+    if (c->k < 1 || c->k > 127)
+        return bad("k must be in [1, 127]");
+    if (c->g < 2 * c->k || c->g > 4096)
+        return bad("g must be in [2k, 4096]");
+    if (c->r < 2 || c->r > 8)
+        return bad("r must be in [2, 8]");
+    if (c->c < 1 || c->c > 16 || c->u > 8 || c->c + c->u > 24)
+        return bad("need 1 <= c <= 16, u <= 8, c + u <= 24");
+    const uint32_t W = 32 - c->u;
+    if (c->c > W || c->s < 1 || c->s > c->c || c->s * (c->r - 1) >= W) {
+        snprintf(buf, sizeof buf, "need c <= 32-u, 1 <= s <= c and s*(r-1) < 32-u (c=%u s=%u r=%u u=%u)", c->c, c->s,
+                 c->r, c->u);
+        why = buf;
+        return ASSE_EINVAL;
+    }
+    if (c->c + c->s * (c->r - 1) < W)
+        return bad("column windows do not cover LBS: need c + s*(r-1) >= 32-u (completeness, Sec. 4.1)");
+    if (c->A < 2)
+        return bad("A must be in [2, 2^32)");
+    if ((c->bh_a & 1) == 0)
+        return bad("bh_a must be odd");
+    if (c->theta < 1)
+        return bad("theta must be >= 1");
+    return ASSE_OK;
+}
+
+// Fields [lo, hi) of ACT block b.
+void block_fields(const asse_pool *p, uint32_t b, uint32_t &lo, uint32_t &hi)
+{
+    const uint32_t k2 = 2 * p->cfg.k;
+    lo = b * p->blk;
+    hi = (b == k2 - 1) ? p->cfg.g : (b + 1) * p->blk;
+}
+
+// Words holding the two ACT blocks that Algorithm 2 checks when slice t_new
+// opens: the blocks whose ACT becomes 0 and k.
+Refresh make_refresh(const asse_pool *p, uint64_t t_new)
+{
+    const uint32_t k = p->cfg.k, k2 = 2 * k;
+    Refresh R{};
+    R.c0n = (uint32_t)(t_new % k2);
+    const uint32_t b[2] = {(k2 - R.c0n) % k2, (k + k2 - R.c0n) % k2};
+    uint32_t lo[2], hi[2];
+    for (int i = 0; i < 2; i++) {
+        uint32_t flo, fhi;
+        block_fields(p, b[i], flo, fhi);
+        lo[i] = flo / p->F;
+        hi[i] = (fhi - 1) / p->F;
+    }
+    if (lo[1] < lo[0]) {
+        std::swap(lo[0], lo[1]);
+        std::swap(hi[0], hi[1]);
+    }
+    if (lo[1] <= hi[0] + 1) {
+        R.q_lo[0] = lo[0];
+        R.q_hi[0] = hi[1] > hi[0] ? hi[1] : hi[0];
+        R.n_ranges = 1;
+    } else {
+        R.q_lo[0] = lo[0]; R.q_hi[0] = hi[0];
+        R.q_lo[1] = lo[1]; R.q_hi[1] = hi[1];
+        R.n_ranges = 2;
+    }
+    return R;
+}
+
+ScanOut scan_out(asse_pool *p)
+{
+    ScanOut o;
+    o.cnt = p->cnt;
+    o.aat = p->aat;
+    o.sa_n = p->sa_n;
+    o.sa_x = p->sa_x;
+    o.sa_mask = p->sa_mask;
+    o.status = p->status;
+    return o;
+}
+
+__global__ void init_pool_kernel(uint32_t *pool, uint64_t nwords, uint32_t Wd, uint32_t words_used,
+                                 uint32_t full_word, uint32_t last_word)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) {
+        const uint32_t q = (uint32_t)(i % Wd);
+        pool[i] = q + 1 < words_used ? full_word : (q + 1 == words_used ? last_word : 0u);
+    }
+}
+
+int reset_close_state(asse_pool *p)
+{
+    const size_t nseg = (size_t)p->cfg.r * p->P.nf;
+    CK(p, cudaMemsetAsync(p->aat, 0, nseg * sizeof(unsigned long long), p->stream));
+    CK(p, cudaMemsetAsync(p->sa_n, 0, nseg * sizeof(uint32_t), p->stream));
+    CK(p, cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream));
+    return ASSE_OK;
+}
+
+int check_kp(asse_pool *p, uint32_t kp)
+{
+    if (kp < 1 || kp > p->cfg.k)
+        return fail(p, ASSE_EINVAL, "kp must be in [1, k]");
+    return ASSE_OK;
+}
+
+int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where)
+{
+    if (!p || !n_out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    if (!p->restored)
+        return fail(p, ASSE_ESTATE, "no restore since the last scan");
+    CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    const Status st = *p->status_host;
+    if (st.overflow) {
+        *n_out = st.needed;
+        char buf[200];
+        snprintf(buf, sizeof buf, "restore needed %llu column tuples in one frame, restore_cap is %u",
+                 (unsigned long long)st.needed, p->cap);
+        return fail(p, ASSE_ECAPACITY, buf);
+    }
+    const uint64_t n = reported ? st.n_report : st.n_csip;
+    *n_out = n;
+    const uint64_t m = n < cap ? n : cap;
+    if (m > 0) {
+        if (!out)
+            return fail(p, ASSE_EINVAL, "out is NULL");
+        CK(p, cudaMemcpyAsync(out, reported ? p->report : p->csip, m * sizeof(asse_superpoint),
+                              where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+        if (where != ASSE_DEVICE)
+            CK(p, cudaStreamSynchronize(p->stream));
+    }
+    if (n > cap)
+        return fail(p, ASSE_ECAPACITY, "output capacity smaller than the list");
+    return ASSE_OK;
+}
+
+void free_all(asse_pool *p)
+{
+    cudaFree(p->pool);
+    cudaFree(p->cnt);
+    cudaFree(p->aat);
+    cudaFree(p->sa_n);
+    cudaFree(p->sa_x);
+    cudaFree(p->sa_mask);
+    cudaFree(p->scratch);
+    cudaFree(p->csip);
+    cudaFree(p->report);
+    cudaFree(p->status);
+    cudaFree(p->stage[0]);
+    cudaFree(p->stage[1]);
+    cudaFree(p->q_aips);
+    cudaFree(p->q_out);
+    if (p->status_host)
+        cudaFreeHost(p->status_host);
+    for (int i = 0; i < 2; i++) {
+        if (p->copied[i])
+            cudaEventDestroy(p->copied[i]);
+        if (p->consumed[i])
+            cudaEventDestroy(p->consumed[i]);
+    }
+    if (p->copy_stream)
+        cudaStreamDestroy(p->copy_stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *asse_strerror(int status)
+{
+    switch (status) {
+    case ASSE_OK: return "ASSE_OK";
+    case ASSE_EINVAL: return "ASSE_EINVAL";
+    case ASSE_ENOMEM: return "ASSE_ENOMEM";
+    case ASSE_ECAPACITY: return "ASSE_ECAPACITY";
+    case ASSE_ECUDA: return "ASSE_ECUDA";
+    case ASSE_ESTATE: return "ASSE_ESTATE";
+    default: return "unknown status";
+    }
+}
+
+const char *asse_last_error(const asse_pool *pool)
+{
+    return pool ? pool->err.c_str() : g_create_error.c_str();
+}
+
+uint64_t asse_launches(const asse_pool *pool) { return pool ? pool->launches : 0; }
+
+int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
+{
+    if (!out)
+        return fail(nullptr, ASSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (validate(cfg, why) != ASSE_OK)
+        return fail(nullptr, ASSE_EINVAL, why);
+    asse_pool *p = new (std::nothrow) asse_pool();
+    if (!p)
+        return fail(nullptr, ASSE_ENOMEM, "host allocation failed");
+    p->cfg = *cfg;
+    p->stream = (cudaStream_t)stream;
+    const uint32_t k = cfg->k;
+    const bool ace = cfg->counter == ASSE_COUNTER_ACE;
+    p->w = ace ? (k == 1 ? 1 : ceil_log2(k + 1)) : ceil_log2(2 * k + 1);
+    p->F = 32 / p->w;
+    p->words_used = (cfg->g + p->F - 1) / p->F;
+    const uint32_t Wd = (p->words_used + 7) / 8 * 8;
+    p->blk = cfg->g / (2 * k);
+    Params &P = p->P;
+    P.k = k;
+    P.k2 = 2 * k;
+    P.g = cfg->g;
+    P.r = cfg->r;
+    P.c = cfg->c;
+    P.u = cfg->u;
+    P.W = 32 - cfg->u;
+    P.E_log2 = cfg->c + cfg->u;
+    P.Wd = Wd;
+    P.A = cfg->A;
+    P.cmask = (1u << cfg->c) - 1;
+    P.theta = cfg->theta;
+    const double g = (double)cfg->g;
+    P.T = (uint32_t)std::ceil(g - g * std::exp(-(double)cfg->theta / g));
+    P.ace = ace ? 1 : 0;
+    P.nf = 1u << cfg->u;
+    P.mw = (cfg->g + 31) / 32;
+    P.blk_magic = ((1ull << 32) + p->blk - 1) / p->blk;
+    P.Ainv = inverse_mod(cfg->A, 4294967311ull);
+    P.bh_a = cfg->bh_a;
+    P.bh_b = cfg->bh_b;
+    for (uint32_t i = 0; i < 8; i++)
+        P.xshift[i] = i < cfg->r ? 2 * P.W - cfg->c - cfg->s * i : 0;
+    p->cap = cfg->restore_cap ? cfg->restore_cap : 4096;
+    p->out_cap = (uint64_t)p->cap * P.nf;
+    p->stage_pairs = cfg->max_batch ? (cfg->max_batch + 1) / 2 * 2 : (4ull << 20);
+
+    const uint64_t n_atv = (uint64_t)cfg->r << P.E_log2;
+    p->pool_words = n_atv * Wd;
+    const size_t nseg = (size_t)cfg->r * P.nf;
+    const size_t slots = (size_t)cfg->r << P.E_log2;  // super-ATV slots: every ATV of a row-frame
+    cudaError_t e = cudaSuccess;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+        delete p;
+        return cuda_fail(nullptr, e, "cudaGetDevice/cudaDeviceGetAttribute");
+    }
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess)
+            e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void **)&p->pool, p->pool_words * 4);
+    alloc((void **)&p->cnt, n_atv * sizeof(uint16_t));
+    alloc((void **)&p->aat, nseg * sizeof(unsigned long long));
+    alloc((void **)&p->sa_n, nseg * sizeof(uint32_t));
+    alloc((void **)&p->sa_x, slots * sizeof(uint32_t));
+    alloc((void **)&p->sa_mask, slots * P.mw * sizeof(uint32_t));
+    alloc((void **)&p->scratch, (size_t)P.nf * 2 * p->cap * sizeof(Tuple));
+    alloc((void **)&p->csip, p->out_cap * sizeof(asse_superpoint));
+    alloc((void **)&p->report, p->out_cap * sizeof(asse_superpoint));
+    alloc((void **)&p->status, sizeof(Status));
+    alloc((void **)&p->stage[0], p->stage_pairs * 8);
+    alloc((void **)&p->stage[1], p->stage_pairs * 8);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&p->status_host, sizeof(Status));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        e = cudaEventCreateWithFlags(&p->copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&p->consumed[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        cudaGetLastError();
+        free_all(p);
+        delete p;
+        return oom ? fail(nullptr, ASSE_ENOMEM, "device allocation failed")
+                   : cuda_fail(nullptr, e, "asse_create");
+    }
+    // InitAT: every field of every ATV at its inactive value (2k, or 0 for
+    // aging counters); fields past g and padding words hold 0.
+    const uint32_t fill = ace ? 0u : 2 * k;
+    uint32_t full_word = 0, last_word = 0;
+    for (uint32_t j = 0; j < p->F; j++) {
+        full_word |= fill << (j * p->w);
+        if ((p->words_used - 1) * p->F + j < cfg->g)
+            last_word |= fill << (j * p->w);
+    }
+    init_pool_kernel<<<p->sms * 4, 256, 0, p->stream>>>(p->pool, p->pool_words, Wd, p->words_used, full_word,
+                                                          last_word);
+    p->launches++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return cuda_fail(nullptr, e, "pool initialisation");
+    }
+    *out = p;
+    return ASSE_OK;
+}
+
+void asse_destroy(asse_pool *pool)
+{
+    if (!pool)
+        return;
+    cudaStreamSynchronize(pool->stream);
+    cudaStreamSynchronize(pool->copy_stream);
+    free_all(pool);
+    delete pool;
+}
+
+int asse_set_stream(asse_pool *pool, void *stream)
+{
+    if (!pool)
+        return ASSE_EINVAL;
+    pool->stream = (cudaStream_t)stream;
+    return ASSE_OK;
+}
+
+int asse_ingest(asse_pool *p, const uint32_t *pairs, uint64_t n, int where)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (n == 0)
+        return ASSE_OK;
+    if (!pairs)
+        return fail(p, ASSE_EINVAL, "pairs is NULL");
+    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
+    p->ingested = 1;  // the pool no longer matches the last scan
+    if (where == ASSE_DEVICE) {
+        if (((uintptr_t)pairs & 15) != 0)
+            return fail(p, ASSE_EINVAL, "device pairs must be 16-byte aligned");
+        CK(p, launch_ingest(p->P, p->w, p->pool, pairs, n, c0, p->sms, p->stream, &p->launches));
+        return ASSE_OK;
+    }
+    if (where != ASSE_HOST)
+        return fail(p, ASSE_EINVAL, "where must be ASSE_HOST or ASSE_DEVICE");
+    // Double-buffered staging (Sec. 4.4): the copy of chunk i+1 runs on the
+    // copy stream while chunk i is ingested on the pool's stream.
+    int last = -1;
+    for (uint64_t off = 0, i = 0; off < n; off += p->stage_pairs, i++) {
+        const int b = (int)(i & 1);
+        const uint64_t m = (n - off) < p->stage_pairs ? (n - off) : p->stage_pairs;
+        CK(p, cudaStreamWaitEvent(p->copy_stream, p->consumed[b], 0));
+        CK(p, cudaMemcpyAsync(p->stage[b], pairs + 2 * off, m * 8, cudaMemcpyHostToDevice, p->copy_stream));
+        CK(p, cudaEventRecord(p->copied[b], p->copy_stream));
+        CK(p, cudaStreamWaitEvent(p->stream, p->copied[b], 0));
+        CK(p, launch_ingest(p->P, p->w, p->pool, p->stage[b], m, c0, p->sms, p->stream, &p->launches));
+        CK(p, cudaEventRecord(p->consumed[b], p->stream));
+        last = b;
+    }
+    // the caller may reuse its host buffer once every chunk has been copied
+    if (last >= 0)
+        CK(p, cudaEventSynchronize(p->copied[last]));
+    return ASSE_OK;
+}
+
+int asse_scan(asse_pool *p, uint32_t kp)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (int rc = check_kp(p, kp))
+        return rc;
+    if (int rc = reset_close_state(p))
+        return rc;
+    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
+    CK(p, launch_scan(p->P, p->w, p->pool, c0, kp, nullptr, scan_out(p), p->sms, p->stream, &p->launches));
+    p->scanned = 1;
+    p->refreshed = 0;
+    p->restored = 0;
+    p->ingested = 0;
+    p->scan_kp = kp;
+    p->scan_slice = p->t;
+    return ASSE_OK;
+}
+
+int asse_restore(asse_pool *p)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (!p->scanned)
+        return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
+    CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
+                         &p->launches));
+    p->restored = 1;
+    return ASSE_OK;
+}
+
+int asse_advance(asse_pool *p)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    const Refresh R = make_refresh(p, p->t + 1);
+    CK(p, launch_refresh(p->P, p->w, p->pool, R, p->sms, p->stream, &p->launches));
+    p->t += 1;
+    p->refreshed = 1;
+    return ASSE_OK;
+}
+
+int asse_close_slice(asse_pool *p, uint32_t kp)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (int rc = check_kp(p, kp))
+        return rc;
+    if (int rc = reset_close_state(p))
+        return rc;
+    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
+    const Refresh R = make_refresh(p, p->t + 1);
+    CK(p, launch_scan(p->P, p->w, p->pool, c0, kp, &R, scan_out(p), p->sms, p->stream, &p->launches));
+    CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
+                         &p->launches));
+    p->scanned = 1;
+    p->restored = 1;
+    p->refreshed = 1;
+    p->scan_kp = kp;
+    p->scan_slice = p->t;
+    p->t += 1;
+    return ASSE_OK;
+}
+
+int asse_estimate(asse_pool *p, const uint32_t *aips, uint64_t n, asse_superpoint *out, int where)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (!p->scanned || p->refreshed || p->ingested || p->scan_slice != p->t)
+        return fail(p, ASSE_ESTATE, "estimate needs a scan of the open slice and no refresh since");
+    if (n == 0)
+        return ASSE_OK;
+    if (!aips || !out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
+    if (where == ASSE_DEVICE) {
+        CK(p, launch_estimate(p->P, p->w, p->pool, c0, p->scan_kp, p->aat, aips, n, out, p->sms, p->stream,
+                              &p->launches));
+        return ASSE_OK;
+    }
+    if (n > p->q_cap) {
+        cudaFree(p->q_aips);
+        cudaFree(p->q_out);
+        p->q_aips = nullptr;
+        p->q_out = nullptr;
+        p->q_cap = 0;
+        CK(p, cudaMalloc((void **)&p->q_aips, n * sizeof(uint32_t)));
+        CK(p, cudaMalloc((void **)&p->q_out, n * sizeof(asse_superpoint)));
+        p->q_cap = n;
+    }
+    CK(p, cudaMemcpyAsync(p->q_aips, aips, n * sizeof(uint32_t), cudaMemcpyHostToDevice, p->stream));
+    CK(p, launch_estimate(p->P, p->w, p->pool, c0, p->scan_kp, p->aat, p->q_aips, n, p->q_out, p->sms, p->stream,
+                          &p->launches));
+    CK(p, cudaMemcpyAsync(out, p->q_out, n * sizeof(asse_superpoint), cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    return ASSE_OK;
+}
+
+int asse_report(asse_pool *p, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where)
+{
+    return read_list(p, true, out, cap, n_out, where);
+}
+
+int asse_candidates(asse_pool *p, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where)
+{
+    return read_list(p, false, out, cap, n_out, where);
+}
+
+int asse_counts(asse_pool *p, uint16_t *out, int where)
+{
+    if (!p || !out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    if (!p->scanned)
+        return fail(p, ASSE_ESTATE, "no scan");
+    const size_t bytes = ((size_t)p->cfg.r << p->P.E_log2) * sizeof(uint16_t);
+    CK(p, cudaMemcpyAsync(out, p->cnt, bytes,
+                          where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (where != ASSE_DEVICE)
+        CK(p, cudaStreamSynchronize(p->stream));
+    return ASSE_OK;
+}
+
+int asse_loads(asse_pool *p, uint64_t *out)
+{
+    if (!p || !out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    if (!p->scanned)
+        return fail(p, ASSE_ESTATE, "no scan");
+    CK(p, cudaMemcpyAsync(out, p->aat, (size_t)p->cfg.r * p->P.nf * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                          p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    return ASSE_OK;
+}
+
+int asse_info(const asse_pool *p, asse_pool_info *out)
+{
+    if (!p || !out)
+        return ASSE_EINVAL;
+    out->w = p->w;
+    out->fields = p->F;
+    out->words = p->P.Wd;
+    out->E = 1u << p->P.E_log2;
+    out->threshold = p->P.T;
+    out->block = p->blk;
+    out->slice = p->t;
+    out->pool_words = p->pool_words;
+    out->pool = p->pool;
+    return ASSE_OK;
+}
+
+int asse_read_pool(asse_pool *p, uint32_t *out, int where)
+{
+    if (!p || !out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    CK(p, cudaMemcpyAsync(out, p->pool, p->pool_words * 4,
+                          where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (where != ASSE_DEVICE)
+        CK(p, cudaStreamSynchronize(p->stream));
+    return ASSE_OK;
+}
+
+int asse_snapshot(asse_pool *p, void *dst, uint64_t cap, uint64_t *n_out)
+{
+    if (!p || !n_out)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    const uint64_t need = sizeof(SnapHeader) + p->pool_words * 4;
+    *n_out = need;
+    if (!dst)
+        return ASSE_OK;
+    if (cap < need)
+        return fail(p, ASSE_ECAPACITY, "snapshot buffer too small");
+    SnapHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "ASSEPOOL", 8);
+    h.version = 1;
+    h.header_bytes = sizeof(SnapHeader);
+    h.cfg = p->cfg;
+    h.slice = p->t;
+    h.pool_words = p->pool_words;
+    h.w = p->w;
+    h.words = p->P.Wd;
+    memcpy(dst, &h, sizeof h);
+    CK(p, cudaMemcpyAsync((char *)dst + sizeof h, p->pool, p->pool_words * 4, cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    return ASSE_OK;
+}
+
+int asse_load(asse_pool *p, const void *src, uint64_t n)
+{
+    if (!p || !src)
+        return fail(p, ASSE_EINVAL, "NULL argument");
+    SnapHeader h;
+    if (n < sizeof h)
+        return fail(p, ASSE_EINVAL, "image too small");
+    memcpy(&h, src, sizeof h);
+    if (memcmp(h.magic, "ASSEPOOL", 8) != 0 || h.version != 1 || h.header_bytes != sizeof h)
+        return fail(p, ASSE_EINVAL, "not an ASSE pool image");
+    const asse_config &a = h.cfg, &b = p->cfg;
+    if (a.k != b.k || a.theta != b.theta || a.g != b.g || a.r != b.r || a.c != b.c || a.u != b.u || a.s != b.s ||
+        a.A != b.A || a.bh_a != b.bh_a || a.bh_b != b.bh_b || a.counter != b.counter ||
+        h.pool_words != p->pool_words || h.w != p->w || h.words != p->P.Wd)
+        return fail(p, ASSE_EINVAL, "image was written by a pool with another configuration");
+    if (n < sizeof h + p->pool_words * 4)
+        return fail(p, ASSE_EINVAL, "image truncated");
+    CK(p, cudaMemcpyAsync(p->pool, (const char *)src + sizeof h, p->pool_words * 4, cudaMemcpyHostToDevice,
+                          p->stream));
+    CK(p, cudaStreamSynchronize(p->stream));
+    p->t = h.slice;
+    p->scanned = p->restored = p->refreshed = 0;
+    return ASSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same
+seeded inputs: the AT pool state bit-exact after every ingest and every
+refresh, per-ATV counts and row-frame loads exact, candidate and report sets
+exact, NAT exact, Eq. 4 estimates within 1e-5 relative."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import check_close, compare_lists, mixed_pairs, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1807_01527_gb300 import asse, build
+    build.build()
+    oracle.build()
+    return asse, oracle, torch
+
+
+def _params(k, g, r, c, u, s, theta, seed=1):
+    return dict(k=k, theta=theta, g=g, r=r, c=c, u=u, s=s, **synth.method_keys(seed))
+
+
+def test_tiny_b_every_slice(mods):
+    """Tiny workload with per-host bip sets (k=4, 16 slices of 65,536 pairs)."""
+    asse, oracle, torch = mods
+    w = synth.workload("tiny_b")
+    pool = asse.Pool(w.params)
+    orc = oracle.Oracle.from_params(w.params)
+    for t in range(w.slices):
+        pairs = w.pairs(t)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        res = check_close(pool, orc, w.k)
+        assert set(w.planted_aip.tolist()) <= {a for a, e, _n in res["report"]}
+        orc.advance()
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+    pool.close()
+
+
+def test_tiny_saturated_state_and_capacity(mods):
+    """Tiny workload as specified (bips uniform over 2^24): the pool
+    saturates, every ATV is super, and the restore must report that it needs
+    more than restore_cap tuples instead of returning a partial list."""
+    asse, oracle, torch = mods
+    w = synth.workload("tiny")
+    pool = asse.Pool(w.params)
+    orc = oracle.Oracle.from_params(w.params)
+    for t in range(6):
+        pairs = w.pairs(t)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(pool.state(), orc.at())
+        cnt = orc.counts(w.k)
+        pool.close_slice(w.k)
+        np.testing.assert_array_equal(pool.counts(), cnt)
+        np.testing.assert_array_equal(pool.loads(), orc.aat(cnt))
+        n_orc, _ = orc.restore(cnt, pool.cap, limit_extra=0)
+        if n_orc > pool.cap:
+            with pytest.raises(asse.AsseError) as ei:
+                pool.report()
+            assert ei.value.status == asse.ECAPACITY and ei.value.n_needed > pool.cap
+        orc.advance()
+        np.testing.assert_array_equal(pool.state(), orc.at())
+
+
+# (k, g, r, c, u, s, counter): every counter width 1..8, r from 2 to 8,
+# frames 1..16, g not a multiple of the fields per word
+CASES = [
+    (1, 37, 4, 8, 0, 8, "at"), (2, 29, 4, 8, 0, 8, "at"), (3, 61, 3, 11, 1, 10, "at"),
+    (5, 130, 5, 7, 1, 6, "at"), (10, 211, 4, 9, 2, 7, "at"), (20, 97, 8, 6, 2, 4, "at"),
+    (40, 257, 4, 8, 0, 8, "at"), (100, 333, 2, 16, 0, 16, "at"),
+    (1, 64, 4, 8, 0, 8, "ace"), (3, 50, 4, 9, 2, 7, "ace"), (5, 77, 5, 7, 1, 6, "ace"),
+    (10, 128, 4, 8, 0, 8, "ace"), (20, 101, 3, 11, 1, 10, "ace"), (40, 300, 4, 8, 0, 8, "ace"),
+    (100, 250, 4, 8, 0, 8, "ace"),
+]
+
+
+@pytest.mark.parametrize("k,g,r,c,u,s,counter", CASES)
+def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
+    asse, oracle, torch = mods
+    theta = max(4, g // 3)
+    p = _params(k, g, r, c, u, s, theta, seed=k + g)
+    mode = 1 if counter == "ace" else 0
+    pool = asse.Pool(p, counter=counter, restore_cap=1 << 14)
+    orc = oracle.Oracle.from_params(p, mode=mode)
+    heavy = [theta // 2, theta, 2 * theta, 3 * theta]
+    n_slices = min(2 * k + 3, 40) if k > 10 else 2 * k + 3
+    rng = np.random.default_rng(k * 31 + g)
+    for t in range(n_slices):
+        n = int(rng.integers(0, 3000)) | 1 if t % 5 else int(rng.integers(0, 3))
+        pairs = mixed_pairs(k + g, t, n, heavy)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        kp = k if t % 3 else 1 + (t % k)
+        check_close(pool, orc, kp)
+        orc.advance()
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+    pool.close()
+
+
+def test_stepwise_equals_fused_and_estimate(mods):
+    """scan -> restore -> estimate -> advance gives the fused close's results,
+    and the estimate of any host equals the oracle's Algorithm 5 + Eq. 4."""
+    asse, oracle, torch = mods
+    p = _params(6, 150, 4, 9, 2, 7, 60, seed=5)
+    fused = asse.Pool(p)
+    step = asse.Pool(p)
+    orc = oracle.Oracle.from_params(p)
+    for t in range(16):
+        pairs = mixed_pairs(5, t, 4001, [30, 60, 120, 400])
+        for pl in (fused, step):
+            pl.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        kp = 1 + t % 6
+        step.scan(kp)
+        step.restore()
+        cnt = orc.counts(kp)
+        aat = orc.aat(cnt)
+        hosts = np.unique(pairs[:, 0])[:50]
+        est = step.estimate(hosts)
+        for row in est:
+            e2, n2 = orc.estimate(aat, int(row["aip"]), kp)
+            assert row["nat"] == n2
+            assert abs(row["est"] - e2) <= 1e-5 * abs(e2) + 1e-6 or (np.isinf(e2) and np.isinf(row["est"]))
+        res = orc.close_report(kp)
+        step.advance()
+        fused.close_slice(kp)
+        for pl in (fused, step):
+            np.testing.assert_array_equal(pl.counts(), res["counts"])
+            compare_lists(pl.candidates(), res["candidates"], p["theta"], "csip")
+        orc.advance()
+        np.testing.assert_array_equal(fused.read_pool(), step.read_pool())
+        np.testing.assert_array_equal(fused.state(), orc.at())
+
+
+def test_host_ingest_chunks_and_snapshot(mods):
+    """Host input copied in several double-buffered chunks equals device
+    input; a snapshot restored into a fresh pool continues identically."""
+    asse, oracle, torch = mods
+    p = _params(4, 128, 4, 10, 0, 8, 64, seed=3)
+    a = asse.Pool(p, max_batch=1001)
+    b = asse.Pool(p)
+    for t in range(5):
+        pairs = mixed_pairs(3, t, 9999, [100, 200])
+        a.ingest(pairs)                  # numpy: host path, 10 chunks
+        b.ingest(to_device(pairs))
+        np.testing.assert_array_equal(a.read_pool(), b.read_pool())
+        a.close_slice()
+        b.close_slice()
+    img = a.snapshot()
+    c = asse.Pool(p)
+    c.load(img)
+    assert c.info()["slice"] == a.info()["slice"] == 5
+    for t in range(5, 9):
+        pairs = mixed_pairs(3, t, 5000, [100, 200])
+        for pl in (a, c):
+            pl.ingest(to_device(pairs))
+            pl.close_slice()
+        np.testing.assert_array_equal(a.read_pool(), c.read_pool())
+        assert sorted(a.report()["aip"].tolist()) == sorted(c.report()["aip"].tolist())
+    bad = asse.Pool(_params(5, 128, 4, 10, 0, 8, 64, seed=3))
+    with pytest.raises(asse.AsseError) as ei:
+        bad.load(img)
+    assert ei.value.status == asse.EINVAL
+
+
+def test_edge_cases(mods):
+    asse, oracle, torch = mods
+    p = _params(3, 40, 4, 8, 0, 8, 10, seed=9)
+    pool = asse.Pool(p, restore_cap=8)
+    orc = oracle.Oracle.from_params(p)
+    pool.close_slice()                          # empty slice
+    assert pool.report().size == 0 and pool.candidates().size == 0
+    orc.advance()
+    one = mixed_pairs(9, 0, 1, [5])
+    pool.ingest(to_device(one))                 # a single pair (tail path only)
+    orc.ingest(one)
+    np.testing.assert_array_equal(pool.state(), orc.at())
+    pool.ingest(one[:0])                        # empty batch
+    with pytest.raises(asse.AsseError) as ei:
+        pool.close_slice(4)                     # k' > k
+    assert ei.value.status == asse.EINVAL
+    with pytest.raises(asse.AsseError) as ei:
+        pool.estimate(np.array([1], dtype=np.uint32))   # no scan of this slice
+    assert ei.value.status == asse.ESTATE
+    with pytest.raises(asse.AsseError):
+        pool.ingest(to_device(mixed_pairs(9, 1, 9, [5]))[1:])  # misaligned device pointer
+    # overflow of a tiny restore capacity is reported with the needed size
+    heavy = mixed_pairs(9, 2, 20000, [60] * 40, n_background=0)
+    pool.ingest(to_device(heavy))
+    pool.close_slice()
+    with pytest.raises(asse.AsseError) as ei:
+        pool.report()
+    assert ei.value.status == asse.ECAPACITY and ei.value.n_needed > 8
+
+
+def test_link_full_size_three_slices(mods):
+    """Link-scale workload at full size (k=10, 8 Mi pairs per slice, 4 x
+    65,536 x 512 ATs): state after ingest and after refresh, counts, loads,
+    candidates and report, for the first three slices."""
+    asse, oracle, torch = mods
+    w = synth.workload("link")
+    pool = asse.Pool(w.params)
+    orc = oracle.Oracle.from_params(w.params)
+    for t in range(3):
+        pairs = w.pairs(t)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        check_close(pool, orc, w.k)
+        orc.advance()
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
