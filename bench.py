@@ -55,7 +55,7 @@ class Clocks:
     def __init__(self, path: str, index: int):
         self.path = path
         self.proc = None
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -66,7 +66,9 @@ class Clocks:
         except Exception:
             self.proc = None
 
-    def stop(self) -> dict:
+    def stop(self, t_begin: float, t_end: float) -> dict:
+        """Samples taken inside [t_begin, t_end] (wall clock); if the region
+        was shorter than the sampling period, the samples nearest to it."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -75,24 +77,27 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S")) + float("0." + f[0].split(".")[1])
+                rows.append((ts, float(f[1]), float(f[2]), [n for n, v in zip(names, f[5:9])
+                                                             if v.lower().startswith("active")]))
+            except (ValueError, IndexError):
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if t_begin <= r[0] <= t_end]
+        where = "inside the timed region"
+        if not inside:
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t_begin), abs(r[0] - t_end)))[:3]
+            where = "nearest to the timed region (shorter than the 200 ms sampling period)"
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted({n for r in inside for n in r[3]}), "samples": len(inside), "where": where}
 
 
 def oracle_slice_time(w, ingest_sample: int):
@@ -140,6 +145,37 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def stepwise_breakdown(pool, dev, w, n):
+    """Mean device time of each stage of the stepwise close (scan, restore,
+    refresh) next to the fused close, over n slices."""
+    import torch
+    stream = torch.cuda.current_stream()
+    acc = {"ingest": [], "scan": [], "restore": [], "refresh": [], "fused_close": []}
+    for i in range(n):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(stream)
+        pool.ingest(dev[i % N_SLICES_CYCLED])
+        e[1].record(stream)
+        pool.scan(w.k)
+        e[2].record(stream)
+        pool.restore()
+        e[3].record(stream)
+        pool.advance()
+        e[4].record(stream)
+        pool.report()
+        for name, a, b in (("ingest", 0, 1), ("scan", 1, 2), ("restore", 2, 3), ("refresh", 3, 4)):
+            acc[name].append(e[a].elapsed_time(e[b]))
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        pool.ingest(dev[(i + 1) % N_SLICES_CYCLED])
+        f0.record(stream)
+        pool.close_slice(w.k)
+        f1.record(stream)
+        pool.report()
+        acc["fused_close"].append(f0.elapsed_time(f1))
+    return {k: statistics.mean(v) for k, v in acc.items()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,6 +185,7 @@ def main():
     ap.add_argument("--workload", default="link", choices=["tiny_b", "link", "long"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
+    ap.add_argument("--breakdown", action="store_true", help="also time scan / restore / refresh separately")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -166,6 +203,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    clocks = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else tempfile.gettempdir(),
+                                 "bench_clocks_%d.csv" % rank), local)
 
     # inputs: N_SLICES_CYCLED distinct slices resident in HBM (512 MB for the
     # link workload, more than L2) and the same slices in pinned host memory
@@ -189,12 +229,10 @@ def main():
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     lat = []
     launches0 = pool.launches
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    clocks = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else tempfile.gettempdir(),
-                                 "bench_clocks_%d.csv" % rank), local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    wall0 = time.time()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
@@ -218,7 +256,7 @@ def main():
     launches = pool.launches - launches0
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
+    wall1 = time.time()
     t_ingest = [ev[i][0].elapsed_time(ev[i][1]) / 1e3 for i in range(args.steps)]
     t_close = [ev[i][1].elapsed_time(ev[i][2]) / 1e3 for i in range(args.steps)]
 
@@ -236,6 +274,8 @@ def main():
         d2h += rep.nbytes + 32
     torch.cuda.synchronize()
     e2e_elapsed = time.perf_counter() - t0
+    clk = clocks.stop(wall0, wall1)
+    breakdown = stepwise_breakdown(pool, dev, w, args.warmup) if args.breakdown else None
 
     if world > 1:
         t = torch.tensor([elapsed, e2e_elapsed], dtype=torch.float64, device="cuda")
@@ -277,6 +317,8 @@ def main():
             "reported_per_slice": n_reported / args.steps,
             "clocks": clk,
         }
+        if breakdown:
+            line["breakdown_ms"] = breakdown
         if not args.no_cpu_baseline and world == 1:
             per_slice, text, n = oracle_slice_time(w, args.ref_sample)
             line["cpu_baseline"] = {"value": n / per_slice, "unit": "pkts/s", "cores": 1, "kind": "oracle",
