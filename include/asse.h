@@ -157,6 +157,41 @@ ASSE_API int asse_scan(asse_pool *pool, uint32_t kp);
  * ATVs of the last scan.  Asynchronous.  Errors: ESTATE (no scan), ECUDA. */
 ASSE_API int asse_restore(asse_pool *pool);
 
+/* Size of the fixed restore scratch of asse_restore_static, in column tuples. */
+#define ASSE_STATIC_RESTORE_TUPLES 131072u
+
+/* The restore of asse_restore (Algorithm 4, Algorithm 5 and Eq. 4 on the
+ * super ATVs of the last scan), for callers that cannot allocate device
+ * memory while they run it.  This entry point has no counterpart in the
+ * paper.  A slice-closing loop with a latency budget cannot call cudaMalloc
+ * or cudaFree, since those may synchronise the device and stall the streams
+ * that feed it, and some hosts give all device memory to another allocator
+ * at start-up so that nothing may be allocated later.  This call allocates
+ * nothing and calls no allocating routine: the join's partial column tuples
+ * live in one array of ASSE_STATIC_RESTORE_TUPLES tuples (3 MiB) compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.
+ *
+ *  tuples_per_frame  tuples kept per frame and join level (the role of
+ *                    restore_cap); tuples_per_frame * 2 * 2^u must not exceed
+ *                    ASSE_STATIC_RESTORE_TUPLES, else ASSE_EINVAL.
+ *  candidates, reported  device arrays of cap records each: every restored
+ *                    candidate, and those whose estimate is >= theta, in
+ *                    unspecified order (as asse_candidates / asse_report).
+ *  counters          device array of 4 uint64_t, zeroed by this call and then
+ *                    filled by the kernel: [0] candidates, [1] reported,
+ *                    [2] tuples an overflowing frame needed, [3] non-zero if
+ *                    a frame overflowed tuples_per_frame (the lists are then
+ *                    incomplete).  Counts above cap mean the lists were cut.
+ * Asynchronous on the pool's stream.  The first call on a device (with that
+ * device current) looks up the scratch array's device address and caches it;
+ * make that first call before any stream capture.  Every call shares the one
+ * array: two calls whose kernels overlap on a GPU (different streams or
+ * pools) race on it and must be ordered by the caller.
+ * Errors: EINVAL (NULL or oversized arguments), ESTATE (no scan), ECUDA. */
+ASSE_API int asse_restore_static(asse_pool *pool, uint32_t tuples_per_frame, asse_superpoint *candidates,
+                                 asse_superpoint *reported, uint64_t cap, uint64_t *counters);
+
 /* Stepwise close, part 3: preserveAT (Algorithm 2) on the two ACT blocks of
  * every ATV whose ACT becomes 0 or k in the next slice (AT pool), or the
  * per-slice decrement of every aging counter (ACE pool); then the next

@@ -50,6 +50,7 @@ EXPORTS = {
     "asse_scan": (i32, [vp, u32]),
     "asse_restore": (i32, [vp]),
     "asse_advance": (i32, [vp]),
+    "asse_restore_static": (i32, [vp, u32, vp, vp, u64, vp]),
     "asse_estimate": (i32, [vp, vp, u64, vp, i32]),
     "asse_report": (i32, [vp, vp, u64, ctypes.POINTER(u64), i32]),
     "asse_candidates": (i32, [vp, vp, u64, ctypes.POINTER(u64), i32]),

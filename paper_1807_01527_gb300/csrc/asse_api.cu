@@ -277,6 +277,23 @@ void free_all(asse_pool *p)
 
 }  // namespace
 
+namespace asse {
+
+int pool_restore_view(asse_pool *p, RestoreView *v)
+{
+    if (!p->scanned)
+        return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
+    v->P = p->P;
+    v->o = scan_out(p);
+    v->stream = p->stream;
+    v->launches = &p->launches;
+    return ASSE_OK;
+}
+
+int pool_fail(asse_pool *p, int code, const std::string &msg) { return fail(p, code, msg); }
+
+}  // namespace asse
+
 extern "C" {
 
 const char *asse_strerror(int status)

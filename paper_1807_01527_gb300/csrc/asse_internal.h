@@ -73,4 +73,16 @@ cudaError_t launch_estimate(const Params &P, uint32_t w, const uint32_t *pool, u
                             const unsigned long long *aat, const uint32_t *aips, uint64_t n, asse_superpoint *out,
                             int sms, cudaStream_t s, uint64_t *launches);
 
+// What asse_restore_static (asse_static.cu) needs from a pool: the launch
+// constants, the last scan's outputs and the stream.  Returns ASSE_ESTATE if
+// the pool has no scan to restore from.
+struct RestoreView {
+    Params P;
+    ScanOut o;
+    cudaStream_t stream;
+    uint64_t *launches;
+};
+int pool_restore_view(asse_pool *p, RestoreView *v);
+int pool_fail(asse_pool *p, int code, const std::string &msg);
+
 }  // namespace asse
