@@ -31,6 +31,10 @@ METRIC = "pkts/s AT ingest+SP estimate per slice, p99 slice latency, % of sector
 N_SLICES_CYCLED = 8
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch on the link
+# workload, from the ncu capture summarised in profiles/ingest_link.md (caches
+# flushed by ncu); None for other workloads or once the kernel changes
+INGEST_TRAFFIC_LINK = 202_667_904
 
 
 def workload_desc(w) -> dict:
@@ -176,6 +180,123 @@ def stepwise_breakdown(pool, dev, w, n):
     return {k: statistics.mean(v) for k, v in acc.items()}
 
 
+def gen_batch_gpu(n: int, seed: int, n_hosts: int = 1 << 20, alpha: float = 1.1):
+    """n link-like (aip, bip) pairs generated on the GPU: Zipf(alpha) hosts,
+    each with a bip set of size d drawn with P(D >= d) = 1/d (capped at 2^20).
+    Returns an (n, 2) int32 CUDA tensor."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    ranks = torch.arange(1, n_hosts + 1, device="cuda", dtype=torch.float64)
+    cdf = torch.cumsum(ranks ** (-alpha), 0)
+    cdf /= cdf[-1].clone()
+    rank = torch.searchsorted(cdf, torch.rand(n, generator=g, device="cuda", dtype=torch.float64))
+    m32 = 0xFFFFFFFF
+
+    def mix(x):
+        x = x & m32
+        x = x ^ (x >> 16)
+        x = (x * 0x85EBCA6B) & m32
+        x = x ^ (x >> 13)
+        x = (x * 0xC2B2AE35) & m32
+        return x ^ (x >> 16)
+    aip = mix(rank + seed * 7919)
+    u = (mix(rank ^ 0x2545F491) + 1).double() / 4294967297.0
+    d = torch.clamp(torch.floor(1.0 / u), max=float(1 << 20))
+    j = torch.floor(torch.rand(n, generator=g, device="cuda", dtype=torch.float64) * d).long()
+    bip = mix(mix(aip ^ 0x5BD1E995) + j)
+    out = torch.stack([aip, bip], dim=1)
+    return torch.where(out >= (1 << 31), out - (1 << 32), out).to(torch.int32).contiguous()
+
+
+def run_serve(args):
+    """Serving: 16 independent streams (k in {4,10,30,60}, 2^14..2^18 ATVs per
+    row, g in {128,512,1024}), slice batches of exponential size with mean 4 Mi
+    pairs clipped to [64 Ki, 16 Mi], a 20 GB device-memory budget; every stream
+    always has its next batch ready (closed loop), each batch followed by the
+    close of its slice.  Reports aggregate pairs/s and the p50/p99 device
+    latency from the start of a close to its report in host memory."""
+    import torch
+    from paper_1807_01527_gb300 import asse, build
+    build.build()
+    rng = np.random.default_rng(5)
+    n_streams, slices_per_stream = 16, args.serve_slices
+    streams = []
+    for i in range(n_streams):
+        k = int(rng.choice([4, 10, 30, 60]))
+        g = int(rng.choice([128, 512, 1024]))
+        g = max(g, 2 * k)
+        elog = int(rng.integers(14, 19))
+        c, u, s_ = synth.column_split(elog, 4)
+        p = dict(k=k, theta=g, g=g, r=4, c=c, u=u, s=s_, **synth.method_keys(1000 + i))
+        sizes = np.clip(rng.exponential(4 << 20, size=slices_per_stream), 64 << 10, 16 << 20).astype(np.int64)
+        streams.append((p, sizes))
+    # batches: a few distinct GPU-generated batches per stream, reused across its slices
+    pool_of_batches = {}
+    for i, (p, sizes) in enumerate(streams):
+        uniq = sorted(set(int(x) for x in sizes[:3]))
+        for n in uniq:
+            pool_of_batches[(i, n)] = gen_batch_gpu(n, 31 * i + n % 997)
+    torch.cuda.synchronize()
+
+    def batch_for(i, t):
+        sizes = streams[i][1]
+        n = int(sizes[t])
+        key = (i, n) if (i, n) in pool_of_batches else min((kk for kk in pool_of_batches if kk[0] == i),
+                                                          key=lambda kk: abs(kk[1] - n))
+        return pool_of_batches[key]
+
+    srv = asse.Server(20 << 30)
+    waiting = list(range(n_streams))
+    running = {}
+    lat, pairs_done, deferred, max_open = [], 0, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while waiting or running:
+        while waiting:
+            i = waiting[0]
+            sid = srv.open(streams[i][0], streams[i][0]["k"], max_batch=16 << 20)
+            if sid is None:
+                deferred += 1
+                break
+            waiting.pop(0)
+            running[i] = [sid, 0, 0]          # sid, slices submitted, slices reported
+        max_open = max(max_open, len(running))
+        progressed = False
+        for i in list(running):
+            sid, sub, rep = running[i]
+            if sub < slices_per_stream:
+                b = batch_for(i, sub)
+                if srv.submit(sid, b, close=True):
+                    running[i][1] += 1
+                    pairs_done += b.shape[0]
+                    progressed = True
+            r = srv.poll(sid)
+            if r is not None:
+                lat.append(r[2])
+                running[i][2] += 1
+                progressed = True
+            if running[i][2] == slices_per_stream:
+                srv.close(sid)
+                del running[i]
+        if not progressed:
+            time.sleep(20e-6)
+    srv.sync()
+    wall = time.perf_counter() - t0
+    srv.destroy()
+    lat.sort()
+    line = {"metric": "serving: aggregate pkts/s over 16 streams, p50/p99 slice-close-to-report latency",
+            "value": pairs_done / wall, "unit": "pkts/s", "n_gpus": 1, "higher_is_better": True,
+            "mode": "serve", "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "16 streams, k in {4,10,30,60}, 2^14..2^18 ATVs/row, g in {128,512,1024}, "
+                                   "batches exp(mean 4Mi) clipped [64Ki,16Mi], 20 GB budget",
+                       "slices_per_stream": slices_per_stream},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "what": "device time from the start of a close to its report in host memory"},
+            "pairs": pairs_done, "wall_s": wall, "closes": len(lat), "admission_deferrals": deferred,
+            "max_streams_open": max_open}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,11 +307,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--breakdown", action="store_true", help="also time scan / restore / refresh separately")
+    ap.add_argument("--mode", default="slice", choices=["slice", "serve"],
+                    help="slice: one pool, the headline line; serve: the multi-stream serving loop")
+    ap.add_argument("--serve-slices", type=int, default=12)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.mode == "serve":
+        if rank == 0:
+            run_serve(args)
+        return
     w = synth.workload(args.workload, seed=1 + rank)
     if args.impl == "reference":
         run_reference(args, w)
@@ -213,6 +341,12 @@ def main():
     dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
     pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host]
     n_pairs = [p.shape[0] for p in host]
+    # Algorithm 3 sets r ATs per pair; repeating an identical (aip, bip) pair
+    # within a slice changes nothing, so the work a slice requires is the
+    # 8-byte read of every pair plus one 32-byte sector for each of the r AT
+    # words of every distinct pair
+    n_distinct = [int(np.unique((p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64)).size)
+                  for p in host]
     stream = torch.cuda.current_stream()
     pool = asse.Pool(w.params, stream=stream.cuda_stream)
 
@@ -289,9 +423,8 @@ def main():
         ing = statistics.mean(t_ingest)
         cls = statistics.mean(t_close)
         n_avg = statistics.mean(n_pairs)
-        # ingest, per pair: the 8-byte pair streamed in, plus one 32-byte
-        # sector for each of the r AT words it reads and sets
-        alg_bytes = n_avg * (8 + 32 * w.r)
+        used = [(args.warmup + i) % N_SLICES_CYCLED for i in range(args.steps)]
+        alg_bytes = statistics.mean(8 * n_pairs[j] + 32 * w.r * n_distinct[j] for j in used)
         peak, peak_src = peaks()
         achieved = alg_bytes / ing / 1e9
         lat_ms = sorted(1e3 * x for x in lat)
@@ -308,9 +441,12 @@ def main():
                                  "what": "close_slice call to report on the host"},
             "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * cls},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "ingest",
-                         "peak_source": peak_src,
-                         "bytes_per_pair": 8 + 32 * w.r},
+                         "frac": achieved / peak,
+                         "traffic": INGEST_TRAFFIC_LINK if args.workload == "link" else None,
+                         "traffic_source": "ncu capture, profiles/ingest_link.md", "kernel": "ingest",
+                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
+                         "model": "8 B per pair + 32 B x r per distinct (aip, bip) pair",
+                         "distinct_pair_fraction": statistics.mean(n_distinct[j] / n_pairs[j] for j in used)},
             "e2e": {"value": e2e_pairs / e2e_elapsed, "unit": "pkts/s",
                     "h2d_bytes_per_step": int(8 * n_avg), "d2h_bytes_per_step": int(d2h / args.steps)},
             "gpu_launches": int(launches),

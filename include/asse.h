@@ -66,7 +66,8 @@ extern "C" {
 /* Pool parameters (Sec. 3 and Sec. 4.1).
  *  k       window size in slices (1..127); AT values are 0..2k, 2k inactive.
  *  theta   super-point threshold on the cardinality (Sec. 2.1).
- *  g       ATs per ATV, 2k <= g <= 65535.  The 2k ACT blocks are contiguous:
+ *  g       ATs per ATV, 2k <= g <= 4096 and g <= 512 * floor(32/w) (an ATV
+ *          fits in 512 words).  The 2k ACT blocks are contiguous:
  *          the first 2k-1 hold floor(g/2k) ATs each, the last the rest.
  *  r       rows, 2..8.
  *  c       column-index bits (ATVs per row and frame = 2^c), 1..16.
@@ -132,9 +133,12 @@ ASSE_API int asse_set_stream(asse_pool *pool, void *stream);
  * pairs: n (aip, bip) uint32 pairs, interleaved (aip0, bip0, aip1, ...).
  *   ASSE_DEVICE: a device address, 16-byte aligned, that must stay valid
  *   until the stream reaches this work; nothing is copied.
- *   ASSE_HOST: host memory (pinned for overlap); copied in max_batch chunks
- *   into device staging, the copy of chunk i+1 overlapping the ingest of
- *   chunk i; the host buffer may be reused when the call returns.
+ *   ASSE_HOST: host memory.  Pinned (page-locked, device-mapped) memory with a
+ *   16-byte aligned device mapping is read in place by the kernel over the
+ *   host link; other memory is copied in max_batch chunks into device
+ *   staging, the copy of chunk i+1 overlapping the ingest of chunk i.  Either
+ *   way the host buffer may be reused when the call returns (the call waits
+ *   for the kernel, resp. the last copy).
  * Order and repetition of pairs within a slice do not change the result.
  * Errors: EINVAL (NULL with n > 0, misalignment), ECUDA. */
 ASSE_API int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);

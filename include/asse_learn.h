@@ -1,0 +1,102 @@
+/*
+ * asse_learn.h -- learned per-estimator cardinality model of the GB300 ASSE
+ * library.  The paper has no learned component: Sec. 3 estimates an ATV's
+ * cardinality with the linear-counting formula (Eq. 2), which saturates as
+ * the ATV fills.  This model maps the state of one ATV to its log-cardinality
+ * with a small MLP (features -> 256 -> 256 -> 1, ReLU), trained and run on the
+ * GPU by the library's own BF16-in / FP32-accumulate kernels; Eq. 2 remains
+ * the fallback outside the training range and the baseline it is judged by.
+ *
+ * Conventions as in asse.h (status codes, where = ASSE_HOST / ASSE_DEVICE,
+ * stream-ordered asynchronous work unless stated).
+ *
+ * Feature row of one ATV (ASSE_FEAT bf16 values, the last 12 zero):
+ *   [0]        |ATV|^{k'} / g            (active ATs, Algorithm 1)
+ *   [1 + a]    (active ATs of age a) / g, a = 0..63, age = slices since the
+ *              AT was set (a < k' <= 64)
+ *   [65]       P = |AAT(k',i,j)| / (g 2^c), the load of the ATV's row i and
+ *              frame j (Sec. 4.3)
+ *   [66]       UP of its frame (product of P over the rows)
+ *   [67]       mean of P over the rows of its frame
+ * Target: ln(cardinality).
+ */
+#ifndef ASSE_LEARN_H
+#define ASSE_LEARN_H
+
+#include "asse.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASSE_FEAT 80  /* feature row width */
+#define ASSE_HID 256  /* hidden width */
+/* parameters, in this order, as fp32: W1[HID][FEAT], b1[HID], W2[HID][HID],
+ * b2[HID], w3[HID], b3 */
+#define ASSE_MLP_NPARAMS (ASSE_HID * ASSE_FEAT + ASSE_HID + ASSE_HID * ASSE_HID + ASSE_HID + ASSE_HID + 1)
+
+typedef struct asse_mlp asse_mlp;
+
+/* Synthetic training states shaped like link-scale traffic: each state is
+ * one ATV of g ATs over a window of k slices, holding one host of
+ * cardinality n (log-uniform in [1, 2^n_max_log2], spread over the k slices
+ * with random shares) plus background: every AT is independently set in each
+ * slice with a probability p drawn uniformly in [0, bg_max] per state.  The
+ * host's bips are distinct, so n is exact by construction. */
+typedef struct asse_synth_cfg {
+    uint32_t k, g, r;      /* window (<= 64), ATs per ATV, rows (for UP) */
+    uint32_t n_max_log2;   /* cardinalities up to 2^n_max_log2 (<= 24) */
+    float bg_max;          /* background probability range per AT and slice */
+    uint32_t pad;
+    uint64_t seed;         /* states are a pure function of (seed, index) */
+    uint64_t bh_a, bh_b;   /* BH keys (bh_a odd), as in asse_config */
+} asse_synth_cfg;
+
+/* Feature rows of every ATV of a pool ([r*E][ASSE_FEAT] bf16 as uint16, in
+ * ATV order), for the window and loads of the last asse_scan.  Valid between
+ * asse_scan and asse_advance (the refresh changes the state).  Requires
+ * kp <= 64.  Errors: ESTATE, EINVAL, ECUDA. */
+ASSE_API int asse_features(asse_pool *pool, uint16_t *x_dev);
+
+/* States first .. first+n-1 of a synthetic set: features x_dev [n][FEAT]
+ * bf16, labels log_n_dev [n] = ln(n) and the Eq. 2 estimate of each state's
+ * count lc_dev [n] (a saturated count g is taken as g - 1/2).  All device
+ * buffers; stream-ordered on stream.  Errors: EINVAL, ECUDA. */
+ASSE_API int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uint16_t *x_dev,
+                               float *log_n_dev, float *lc_dev, void *stream);
+
+/* A model with Kaiming-uniform weights drawn from seed and zero biases. */
+ASSE_API int asse_mlp_create(uint64_t seed, void *stream, asse_mlp **out);
+ASSE_API void asse_mlp_destroy(asse_mlp *mlp);
+ASSE_API int asse_mlp_set_stream(asse_mlp *mlp, void *stream);
+
+/* Copy all ASSE_MLP_NPARAMS fp32 parameters to / from host memory
+ * (synchronises). */
+ASSE_API int asse_mlp_get_params(asse_mlp *mlp, float *host);
+ASSE_API int asse_mlp_set_params(asse_mlp *mlp, const float *host);
+
+/* y_dev[i] = model(x_dev[i]) for n feature rows (device buffers). */
+ASSE_API int asse_mlp_forward(asse_mlp *mlp, const uint16_t *x_dev, uint64_t n, float *y_dev);
+
+/* Gradients of the mean squared error (1/n) sum (model(x_i) - t_i)^2 with
+ * respect to every parameter, for n rows (device buffers); loss_dev (may be
+ * NULL) receives the loss.  Does not change the parameters. */
+ASSE_API int asse_mlp_backward(asse_mlp *mlp, const uint16_t *x_dev, const float *t_dev, uint64_t n,
+                               float *loss_dev);
+
+/* Copy the gradients of the last backward / train step to host memory
+ * (ASSE_MLP_NPARAMS fp32, parameter order; synchronises). */
+ASSE_API int asse_mlp_get_grads(asse_mlp *mlp, float *host);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
+ * the gradients of n rows: backward then update. */
+ASSE_API int asse_mlp_train_step(asse_mlp *mlp, const uint16_t *x_dev, const float *t_dev, uint64_t n, float lr,
+                                 float *loss_dev);
+
+/* Message of the last failing call on mlp. */
+ASSE_API const char *asse_mlp_last_error(const asse_mlp *mlp);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASSE_LEARN_H */

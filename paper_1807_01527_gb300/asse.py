@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libasse.so")
 
-OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE = 0, 1, 2, 3, 4, 5
+OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE, EAGAIN = 0, 1, 2, 3, 4, 5, 6
 HOST, DEVICE = 0, 1
 COUNTER_AT, COUNTER_ACE = 0, 1
 SP_SATURATED, SP_REPORTED = 1, 2
@@ -38,7 +38,14 @@ class PoolInfo(ctypes.Structure):
                 ("slice", u64), ("pool_words", u64), ("pool", vp)]
 
 
+class SynthCfg(ctypes.Structure):
+    _fields_ = [("k", u32), ("g", u32), ("r", u32), ("n_max_log2", u32), ("bg_max", ctypes.c_float),
+                ("pad", u32), ("seed", u64), ("bh_a", u64), ("bh_b", u64)]
+
+
 SP_DTYPE = np.dtype([("aip", "<u4"), ("nat", "<u4"), ("est", "<f4"), ("flags", "<u4")])
+FEAT, HID = 80, 256
+MLP_NPARAMS = HID * FEAT + HID + HID * HID + HID + HID + 1
 
 # Every entry point of include/asse.h: name -> (restype, argtypes).
 EXPORTS = {
@@ -63,6 +70,32 @@ EXPORTS = {
     "asse_launches": (u64, [vp]),
     "asse_last_error": (ctypes.c_char_p, [vp]),
     "asse_strerror": (ctypes.c_char_p, [i32]),
+    # include/asse_learn.h
+    "asse_features": (i32, [vp, vp]),
+    "asse_synth_states": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
+    "asse_mlp_create": (i32, [u64, vp, ctypes.POINTER(vp)]),
+    "asse_mlp_destroy": (None, [vp]),
+    "asse_mlp_set_stream": (i32, [vp, vp]),
+    "asse_mlp_get_params": (i32, [vp, vp]),
+    "asse_mlp_set_params": (i32, [vp, vp]),
+    "asse_mlp_forward": (i32, [vp, vp, u64, vp]),
+    "asse_mlp_backward": (i32, [vp, vp, vp, u64, vp]),
+    "asse_mlp_get_grads": (i32, [vp, vp]),
+    "asse_mlp_train_step": (i32, [vp, vp, vp, u64, ctypes.c_float, vp]),
+    "asse_mlp_last_error": (ctypes.c_char_p, [vp]),
+    # include/asse_serve.h
+    "asse_server_create": (i32, [u64, ctypes.POINTER(vp)]),
+    "asse_server_destroy": (None, [vp]),
+    "asse_server_stream_bytes": (u64, [ctypes.POINTER(Config), u64]),
+    "asse_server_bytes_in_use": (u64, [vp]),
+    "asse_server_open": (i32, [vp, ctypes.POINTER(Config), u32, u64, ctypes.POINTER(u32)]),
+    "asse_server_submit": (i32, [vp, u32, vp, u64, i32, i32]),
+    "asse_server_poll": (i32, [vp, u32, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                               ctypes.POINTER(ctypes.c_float)]),
+    "asse_server_sync": (i32, [vp]),
+    "asse_server_close": (i32, [vp, u32]),
+    "asse_server_pool": (vp, [vp, u32]),
+    "asse_server_last_error": (ctypes.c_char_p, [vp]),
 }
 
 _lib = None
@@ -118,6 +151,93 @@ def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
     h = np.arange(g)
     sel = words[:, :, h // F]
     return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
+
+
+def make_config(params: dict, counter: str = "at", restore_cap: int = 0, max_batch: int = 0) -> Config:
+    return Config(int(params["k"]), int(params["theta"]), int(params["g"]), int(params["r"]), int(params["c"]),
+                  int(params["u"]), int(params["s"]), int(params["A"]), int(params["bh_a"]), int(params["bh_b"]),
+                  COUNTER_ACE if counter == "ace" else COUNTER_AT, int(restore_cap), int(max_batch))
+
+
+class Server:
+    """Multi-stream serving loop (include/asse_serve.h)."""
+
+    def __init__(self, budget_bytes: int):
+        self._h = vp()
+        rc = lib().asse_server_create(int(budget_bytes), ctypes.byref(self._h))
+        if rc != OK:
+            raise AsseError(rc, "asse_server_create failed")
+        self.rcap = {}
+
+    def _err(self, rc):
+        return AsseError(rc, lib().asse_server_last_error(self._h).decode())
+
+    def destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().asse_server_destroy(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    @staticmethod
+    def stream_bytes(params: dict, max_batch: int, counter: str = "at", restore_cap: int = 0) -> int:
+        cfg = make_config(params, counter, restore_cap)
+        return int(lib().asse_server_stream_bytes(ctypes.byref(cfg), max_batch))
+
+    def bytes_in_use(self) -> int:
+        return int(lib().asse_server_bytes_in_use(self._h))
+
+    def open(self, params: dict, kp: int, max_batch: int, counter: str = "at", restore_cap: int = 0):
+        """Stream id, or None if it does not fit the budget now."""
+        cfg = make_config(params, counter, restore_cap)
+        sid = u32(0)
+        rc = lib().asse_server_open(self._h, ctypes.byref(cfg), kp, max_batch, ctypes.byref(sid))
+        if rc == ENOMEM:
+            return None
+        if rc != OK:
+            raise self._err(rc)
+        self.rcap[sid.value] = (restore_cap or 4096)
+        return sid.value
+
+    def submit(self, sid: int, pairs, close: bool) -> bool:
+        """False if the stream's report ring is full (poll first)."""
+        if pairs is None:
+            ptr, n, where = None, 0, DEVICE
+        else:
+            ptr, n, where, _keep = _pairs_arg(pairs)
+        rc = lib().asse_server_submit(self._h, sid, vp(ptr), n, where, 1 if close else 0)
+        if rc == EAGAIN:
+            return False
+        if rc != OK:
+            raise self._err(rc)
+        return True
+
+    def poll(self, sid: int):
+        """(report array, slice, latency ms) of the oldest finished close, or None."""
+        cap = self.rcap[sid]
+        buf = np.zeros(cap, dtype=SP_DTYPE)
+        n, sl, ms = u64(0), u64(0), ctypes.c_float(0)
+        rc = lib().asse_server_poll(self._h, sid, vp(buf.ctypes.data), cap, ctypes.byref(n), ctypes.byref(sl),
+                                    ctypes.byref(ms))
+        if rc == EAGAIN:
+            return None
+        if rc != OK:
+            raise self._err(rc)
+        return buf[: n.value], int(sl.value), float(ms.value)
+
+    def sync(self):
+        rc = lib().asse_server_sync(self._h)
+        if rc != OK:
+            raise self._err(rc)
+
+    def close(self, sid: int):
+        rc = lib().asse_server_close(self._h, sid)
+        if rc != OK:
+            raise self._err(rc)
 
 
 class Pool:
@@ -249,3 +369,87 @@ class Pool:
 
     def load(self, image: bytes):
         self._check(lib().asse_load(self._h, image, len(image)))
+
+    def features(self):
+        """Feature rows [r*E][FEAT] (torch bfloat16 on the device) of every
+        ATV, between scan() and advance()."""
+        import torch
+        x = torch.empty((self.r * self._info["E"], FEAT), dtype=torch.bfloat16, device="cuda")
+        self._check(lib().asse_features(self._h, vp(x.data_ptr())))
+        return x
+
+
+def synth_states(cfg: dict, first: int, n: int, stream: int | None = None):
+    """Synthetic training states (include/asse_learn.h): (x [n][FEAT] bf16,
+    ln n [n] fp32, Eq. 2 estimate [n] fp32), torch tensors on the device."""
+    import torch
+    c = SynthCfg(int(cfg["k"]), int(cfg["g"]), int(cfg["r"]), int(cfg.get("n_max_log2", 20)),
+                 float(cfg.get("bg_max", 0.01)), 0, int(cfg["seed"]), int(cfg["bh_a"]), int(cfg["bh_b"]))
+    x = torch.empty((n, FEAT), dtype=torch.bfloat16, device="cuda")
+    ln = torch.empty(n, dtype=torch.float32, device="cuda")
+    lc = torch.empty(n, dtype=torch.float32, device="cuda")
+    rc = lib().asse_synth_states(ctypes.byref(c), first, n, vp(x.data_ptr()), vp(ln.data_ptr()), vp(lc.data_ptr()),
+                                 vp(_current_stream() if stream is None else stream))
+    if rc != OK:
+        raise AsseError(rc, "asse_synth_states failed")
+    return x, ln, lc
+
+
+class MLP:
+    """The learned per-ATV estimator of include/asse_learn.h."""
+
+    def __init__(self, seed: int = 1, stream: int | None = None):
+        self._h = vp()
+        rc = lib().asse_mlp_create(seed, vp(_current_stream() if stream is None else stream), ctypes.byref(self._h))
+        if rc != OK:
+            raise AsseError(rc, "asse_mlp_create failed")
+
+    def _check(self, rc):
+        if rc != OK:
+            raise AsseError(rc, lib().asse_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().asse_mlp_destroy(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        self._check(lib().asse_mlp_get_params(self._h, vp(out.ctypes.data)))
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == MLP_NPARAMS
+        self._check(lib().asse_mlp_set_params(self._h, vp(p.ctypes.data)))
+
+    def grads(self) -> np.ndarray:
+        out = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        self._check(lib().asse_mlp_get_grads(self._h, vp(out.ctypes.data)))
+        return out
+
+    def forward(self, x):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self._check(lib().asse_mlp_forward(self._h, vp(x.data_ptr()), x.shape[0], vp(y.data_ptr())))
+        return y
+
+    def backward(self, x, t):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        self._check(lib().asse_mlp_backward(self._h, vp(x.data_ptr()), vp(t.data_ptr()), x.shape[0],
+                                            vp(loss.data_ptr())))
+        return loss
+
+    def train_step(self, x, t, lr: float):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        self._check(lib().asse_mlp_train_step(self._h, vp(x.data_ptr()), vp(t.data_ptr()), x.shape[0], lr,
+                                              vp(loss.data_ptr())))
+        return loss

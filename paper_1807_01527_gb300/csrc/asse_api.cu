@@ -48,6 +48,7 @@ struct asse_pool {
     uint64_t out_cap = 0;
     Status *status = nullptr;
     Status *status_host = nullptr;
+    SliceCtl *ctl = nullptr;  // device copy of the slice-dependent launch arguments
     uint32_t *stage[2] = {nullptr, nullptr};
     uint64_t stage_pairs = 0;
     uint32_t *q_aips = nullptr;
@@ -135,46 +136,11 @@ int validate(const asse_config *c, std::string &why)
         return bad("bh_a must be odd");
     if (c->theta < 1)
         return bad("theta must be >= 1");
+    // the scan holds one ATV in a warp tile of at most 512 words
+    const uint32_t w = c->counter == ASSE_COUNTER_ACE ? (c->k == 1 ? 1 : ceil_log2(c->k + 1)) : ceil_log2(2 * c->k + 1);
+    if ((c->g + 32 / w - 1) / (32 / w) > 512)
+        return bad("an ATV must fit in 512 words: need g <= 512 * floor(32 / w)");
     return ASSE_OK;
-}
-
-// Fields [lo, hi) of ACT block b.
-void block_fields(const asse_pool *p, uint32_t b, uint32_t &lo, uint32_t &hi)
-{
-    const uint32_t k2 = 2 * p->cfg.k;
-    lo = b * p->blk;
-    hi = (b == k2 - 1) ? p->cfg.g : (b + 1) * p->blk;
-}
-
-// Words holding the two ACT blocks that Algorithm 2 checks when slice t_new
-// opens: the blocks whose ACT becomes 0 and k.
-Refresh make_refresh(const asse_pool *p, uint64_t t_new)
-{
-    const uint32_t k = p->cfg.k, k2 = 2 * k;
-    Refresh R{};
-    R.c0n = (uint32_t)(t_new % k2);
-    const uint32_t b[2] = {(k2 - R.c0n) % k2, (k + k2 - R.c0n) % k2};
-    uint32_t lo[2], hi[2];
-    for (int i = 0; i < 2; i++) {
-        uint32_t flo, fhi;
-        block_fields(p, b[i], flo, fhi);
-        lo[i] = flo / p->F;
-        hi[i] = (fhi - 1) / p->F;
-    }
-    if (lo[1] < lo[0]) {
-        std::swap(lo[0], lo[1]);
-        std::swap(hi[0], hi[1]);
-    }
-    if (lo[1] <= hi[0] + 1) {
-        R.q_lo[0] = lo[0];
-        R.q_hi[0] = hi[1] > hi[0] ? hi[1] : hi[0];
-        R.n_ranges = 1;
-    } else {
-        R.q_lo[0] = lo[0]; R.q_hi[0] = hi[0];
-        R.q_lo[1] = lo[1]; R.q_hi[1] = hi[1];
-        R.n_ranges = 2;
-    }
-    return R;
 }
 
 ScanOut scan_out(asse_pool *p)
@@ -201,10 +167,7 @@ __global__ void init_pool_kernel(uint32_t *pool, uint64_t nwords, uint32_t Wd, u
 
 int reset_close_state(asse_pool *p)
 {
-    const size_t nseg = (size_t)p->cfg.r * p->P.nf;
-    CK(p, cudaMemsetAsync(p->aat, 0, nseg * sizeof(unsigned long long), p->stream));
-    CK(p, cudaMemsetAsync(p->sa_n, 0, nseg * sizeof(uint32_t), p->stream));
-    CK(p, cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream));
+    CK(p, launch_reset(p->aat, p->sa_n, p->cfg.r * p->P.nf, p->status, p->stream, &p->launches));
     return ASSE_OK;
 }
 
@@ -224,6 +187,8 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
     CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     const Status st = *p->status_host;
+    if (st.error)
+        return fail(p, ASSE_ECUDA, "a bounded device wait of the scan gave up (bulk copy did not complete)");
     if (st.overflow) {
         *n_out = st.needed;
         char buf[200];
@@ -259,6 +224,7 @@ void free_all(asse_pool *p)
     cudaFree(p->csip);
     cudaFree(p->report);
     cudaFree(p->status);
+    cudaFree(p->ctl);
     cudaFree(p->stage[0]);
     cudaFree(p->stage[1]);
     cudaFree(p->q_aips);
@@ -291,6 +257,77 @@ int pool_restore_view(asse_pool *p, RestoreView *v)
 }
 
 int pool_fail(asse_pool *p, int code, const std::string &msg) { return fail(p, code, msg); }
+
+int pool_enqueue_close(asse_pool *p, uint32_t kp)
+{
+    if (int rc = reset_close_state(p))
+        return rc;
+    CK(p, launch_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
+                         &p->launches));
+    CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
+    return ASSE_OK;
+}
+
+void pool_after_close(asse_pool *p, uint32_t kp)
+{
+    p->scanned = 1;
+    p->restored = 1;
+    p->refreshed = 1;
+    p->ingested = 0;
+    p->scan_kp = kp;
+    p->scan_slice = p->t;
+    p->t += 1;
+}
+
+int pool_enqueue_ingest(asse_pool *p, const uint32_t *pairs_dev, const unsigned long long *n_dev)
+{
+    CK(p, launch_ingest(p->P, p->w, p->pool, pairs_dev, 0, n_dev, p->ctl, p->sms, p->stream, &p->launches));
+    p->ingested = 1;
+    return ASSE_OK;
+}
+
+PoolBuffers pool_buffers(asse_pool *p)
+{
+    PoolBuffers b;
+    b.status = p->status;
+    b.report = p->report;
+    b.out_cap = p->out_cap;
+    b.stream = p->stream;
+    b.cap = p->cap;
+    return b;
+}
+
+// Device bytes asse_create allocates for cfg (the server's admission unit).
+uint64_t pool_device_bytes(const asse_config *cfg)
+{
+    const bool ace = cfg->counter == ASSE_COUNTER_ACE;
+    const uint32_t w = ace ? (cfg->k == 1 ? 1 : ceil_log2(cfg->k + 1)) : ceil_log2(2 * cfg->k + 1);
+    const uint32_t F = 32 / w;
+    const uint64_t Wd = ((cfg->g + F - 1) / F + 7) / 8 * 8;
+    const uint64_t n_atv = (uint64_t)cfg->r << (cfg->c + cfg->u);
+    const uint64_t nf = 1ull << cfg->u, nseg = cfg->r * nf, mw = (cfg->g + 31) / 32;
+    const uint64_t cap = cfg->restore_cap ? cfg->restore_cap : 4096;
+    const uint64_t stage = cfg->max_batch ? (cfg->max_batch + 1) / 2 * 2 : (4ull << 20);
+    return n_atv * Wd * 4 + n_atv * 2 + nseg * (8 + 4) + n_atv * 4 + n_atv * mw * 4 + nf * 2 * cap * sizeof(Tuple) +
+           2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8;
+}
+
+int pool_feature_view(asse_pool *p, FeatureView *v)
+{
+    if (!p->scanned || p->refreshed || p->ingested || p->scan_slice != p->t)
+        return fail(p, ASSE_ESTATE, "features need a scan of the open slice and no refresh or ingest since");
+    v->P = p->P;
+    v->w = p->w;
+    v->pool = p->pool;
+    v->c0 = (uint32_t)(p->t % (2 * p->cfg.k));
+    v->kp = p->scan_kp;
+    v->aat = p->aat;
+    v->stream = p->stream;
+    v->launches = &p->launches;
+    v->sms = p->sms;
+    return ASSE_OK;
+}
 
 }  // namespace asse
 
@@ -354,6 +391,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     P.ace = ace ? 1 : 0;
     P.nf = 1u << cfg->u;
     P.mw = (cfg->g + 31) / 32;
+    P.blk = p->blk;
+    P.F = p->F;
     P.blk_magic = ((1ull << 32) + p->blk - 1) / p->blk;
     P.Ainv = inverse_mod(cfg->A, 4294967311ull);
     P.bh_a = cfg->bh_a;
@@ -389,6 +428,7 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     alloc((void **)&p->csip, p->out_cap * sizeof(asse_superpoint));
     alloc((void **)&p->report, p->out_cap * sizeof(asse_superpoint));
     alloc((void **)&p->status, sizeof(Status));
+    alloc((void **)&p->ctl, sizeof(SliceCtl));
     alloc((void **)&p->stage[0], p->stage_pairs * 8);
     alloc((void **)&p->stage[1], p->stage_pairs * 8);
     if (e == cudaSuccess)
@@ -423,6 +463,10 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream);
+    const SliceCtl ctl0 = slice_ctl(P, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, p->stream);
+
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
@@ -460,16 +504,28 @@ int asse_ingest(asse_pool *p, const uint32_t *pairs, uint64_t n, int where)
         return ASSE_OK;
     if (!pairs)
         return fail(p, ASSE_EINVAL, "pairs is NULL");
-    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
     p->ingested = 1;  // the pool no longer matches the last scan
     if (where == ASSE_DEVICE) {
         if (((uintptr_t)pairs & 15) != 0)
             return fail(p, ASSE_EINVAL, "device pairs must be 16-byte aligned");
-        CK(p, launch_ingest(p->P, p->w, p->pool, pairs, n, c0, p->sms, p->stream, &p->launches));
+        CK(p, launch_ingest(p->P, p->w, p->pool, pairs, n, nullptr, p->ctl, p->sms, p->stream, &p->launches));
         return ASSE_OK;
     }
     if (where != ASSE_HOST)
         return fail(p, ASSE_EINVAL, "where must be ASSE_HOST or ASSE_DEVICE");
+    // Pinned (page-locked, device-mapped) host memory is read in place by the
+    // kernel over the host link: no staging copy, and the transfer overlaps
+    // the ingest by construction.
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, pairs) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer != nullptr && ((uintptr_t)attr.devicePointer & 15) == 0) {
+        CK(p, launch_ingest(p->P, p->w, p->pool, static_cast<const uint32_t *>(attr.devicePointer), n, nullptr,
+                            p->ctl, p->sms, p->stream, &p->launches));
+        // the caller may reuse its buffer once the kernel has read it
+        CK(p, cudaStreamSynchronize(p->stream));
+        return ASSE_OK;
+    }
+    cudaGetLastError();  // pageable memory: cudaPointerGetAttributes may have set an error
     // Double-buffered staging (Sec. 4.4): the copy of chunk i+1 runs on the
     // copy stream while chunk i is ingested on the pool's stream.
     int last = -1;
@@ -480,7 +536,8 @@ int asse_ingest(asse_pool *p, const uint32_t *pairs, uint64_t n, int where)
         CK(p, cudaMemcpyAsync(p->stage[b], pairs + 2 * off, m * 8, cudaMemcpyHostToDevice, p->copy_stream));
         CK(p, cudaEventRecord(p->copied[b], p->copy_stream));
         CK(p, cudaStreamWaitEvent(p->stream, p->copied[b], 0));
-        CK(p, launch_ingest(p->P, p->w, p->pool, p->stage[b], m, c0, p->sms, p->stream, &p->launches));
+        CK(p, launch_ingest(p->P, p->w, p->pool, p->stage[b], m, nullptr, p->ctl, p->sms, p->stream,
+                            &p->launches));
         CK(p, cudaEventRecord(p->consumed[b], p->stream));
         last = b;
     }
@@ -498,8 +555,7 @@ int asse_scan(asse_pool *p, uint32_t kp)
         return rc;
     if (int rc = reset_close_state(p))
         return rc;
-    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
-    CK(p, launch_scan(p->P, p->w, p->pool, c0, kp, nullptr, scan_out(p), p->sms, p->stream, &p->launches));
+    CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     p->scanned = 1;
     p->refreshed = 0;
     p->restored = 0;
@@ -525,8 +581,8 @@ int asse_advance(asse_pool *p)
 {
     if (!p)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
-    const Refresh R = make_refresh(p, p->t + 1);
-    CK(p, launch_refresh(p->P, p->w, p->pool, R, p->sms, p->stream, &p->launches));
+    CK(p, launch_refresh(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
+    CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
     p->t += 1;
     p->refreshed = 1;
     return ASSE_OK;
@@ -538,19 +594,9 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (int rc = check_kp(p, kp))
         return rc;
-    if (int rc = reset_close_state(p))
+    if (int rc = pool_enqueue_close(p, kp))
         return rc;
-    const uint32_t c0 = (uint32_t)(p->t % (2 * p->cfg.k));
-    const Refresh R = make_refresh(p, p->t + 1);
-    CK(p, launch_scan(p->P, p->w, p->pool, c0, kp, &R, scan_out(p), p->sms, p->stream, &p->launches));
-    CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
-                         &p->launches));
-    p->scanned = 1;
-    p->restored = 1;
-    p->refreshed = 1;
-    p->scan_kp = kp;
-    p->scan_slice = p->t;
-    p->t += 1;
+    pool_after_close(p, kp);
     return ASSE_OK;
 }
 
@@ -696,6 +742,8 @@ int asse_load(asse_pool *p, const void *src, uint64_t n)
         return fail(p, ASSE_EINVAL, "image truncated");
     CK(p, cudaMemcpyAsync(p->pool, (const char *)src + sizeof h, p->pool_words * 4, cudaMemcpyHostToDevice,
                           p->stream));
+    const SliceCtl c = slice_ctl(p->P, h.slice);
+    CK(p, cudaMemcpyAsync(p->ctl, &c, sizeof c, cudaMemcpyHostToDevice, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     p->t = h.slice;
     p->scanned = p->restored = p->refreshed = 0;

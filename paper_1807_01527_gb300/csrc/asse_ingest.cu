@@ -1,10 +1,15 @@
 // K1: Algorithm 3 (Scan IP pair, Sec. 4.1) over a batch of (aip, bip) pairs.
 //
 // One thread takes two pairs per 128-bit streaming load (evict-first, so the
-// pair stream does not push the pool out of L2), computes f(aip), the frame,
-// the r column indices, BH(bip) and the ACT of that AT in registers, issues
-// the r word loads together, then sets the r fields.  A field that already
-// holds the slice's value costs one (usually cached) load and no atomic.
+// pair stream does not push the pool out of L2).  It first computes BH(bip)
+// and looks the key (aip, BH(bip)) up in a direct-mapped table of recently
+// seen keys in shared memory: a pair whose key this block already handled in
+// this launch sets exactly the same r fields to the same values, so it is
+// skipped (SetAT is idempotent within a slice; a slot collision only means a
+// repeat is processed again).  For the other pairs it computes f(aip), the
+// frame, the r column indices and the ACT of the AT in registers, issues the
+// r word loads together, then sets the r fields; a field that already holds
+// the slice's value costs one load and no atomic.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,27 +52,78 @@ __device__ __forceinline__ void set_field(uint32_t *addr, uint32_t old, uint32_t
     }
 }
 
+// f(aip), its frame and LBS twice over (the column windows are shifts of it).
+__device__ __forceinline__ void prep_host(const Params &P, uint32_t aip, uint64_t &LL, uint32_t &z)
+{
+    const uint32_t f = mangle(P.A, aip);
+    z = f & (P.nf - 1);
+    LL = lbs_twice(P, f);
+}
+
 __device__ __forceinline__ uint32_t *field_word(const Params &P, uint32_t *pool, int i, uint32_t z, uint64_t LL,
                                                 uint32_t q)
 {
     return pool + (((uint64_t)i << P.E_log2) + ((z << P.c) | column(P, LL, i))) * P.Wd + q;
 }
 
-template <int WB, int R>
-__global__ void __launch_bounds__(256) ingest_kernel(Params P, uint32_t *pool, const uint4 *__restrict__ pairs,
-                                                     uint64_t nvec, const uint2 *__restrict__ tail, uint32_t c0)
+constexpr int INGEST_THREADS = 1024;
+constexpr int INGEST_BLOCKS_PER_SM = 1;
+constexpr uint32_t SEEN_LOG2 = 14;  // 16,384 keys = 128 KB of shared memory per block
+constexpr unsigned long long NO_KEY = ~0ull;  // BH values are < 2^16, so never a real key
+
+__device__ __forceinline__ uint32_t seen_slot(uint32_t aip, uint32_t h)
 {
+    return (aip * 0x9E3779B1u ^ h * 0x85EBCA77u) >> (32 - SEEN_LOG2);
+}
+
+// True if (aip, h) was recorded in this block's table; records it otherwise.
+__device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t aip, uint32_t h)
+{
+    const unsigned long long key = ((unsigned long long)aip << 32) | h;
+    const uint32_t s = seen_slot(aip, h);
+    if (seen[s] == key)
+        return true;
+    seen[s] = key;
+    return false;
+}
+
+template <int WB, int R>
+__global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
+    ingest_kernel(Params P, uint32_t *pool, const uint32_t *__restrict__ pairs_raw, uint64_t n_arg,
+                  const unsigned long long *n_dev, const SliceCtl *ctl)
+{
+    const uint32_t c0 = ctl->c0;
+    const uint64_t n = n_dev ? *n_dev : n_arg;
+    const uint64_t nvec = n / 2;
+    const uint4 *__restrict__ pairs = reinterpret_cast<const uint4 *>(pairs_raw);
+    const uint2 *__restrict__ tail = (n & 1) ? reinterpret_cast<const uint2 *>(pairs_raw + 2 * (n - 1)) : nullptr;
+    constexpr uint32_t F = 32 / WB;
     constexpr uint32_t FM = (1u << WB) - 1;
     constexpr int RM = R ? R : 8;
+    extern __shared__ unsigned long long seen[];
+    for (uint32_t i = threadIdx.x; i < (1u << SEEN_LOG2); i += blockDim.x)
+        seen[i] = NO_KEY;
+    __syncthreads();
     const int r = R ? R : (int)P.r;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (uint64_t v = tid; v < nvec; v += stride) {
         const uint4 pr = __ldcs(pairs + v);
-        uint64_t LL0, LL1;
-        uint32_t z0, z1, q0, q1, sh0, sh1, val0, val1;
-        prep_pair<WB>(P, c0, pr.x, pr.y, LL0, z0, q0, sh0, val0);
-        prep_pair<WB>(P, c0, pr.z, pr.w, LL1, z1, q1, sh1, val1);
+        const uint32_t h0 = bip_hash(P, pr.y), h1 = bip_hash(P, pr.w);
+        const bool do0 = !seen_before(seen, pr.x, h0);
+        const bool do1 = !seen_before(seen, pr.z, h1);
+        if (!(do0 | do1))
+            continue;
+        uint64_t LL0 = 0, LL1 = 0;
+        uint32_t z0 = 0, z1 = 0, val0 = 0, val1 = 0;
+        if (do0)
+            prep_host(P, pr.x, LL0, z0);
+        if (do1)
+            prep_host(P, pr.z, LL1, z1);
+        val0 = P.ace ? P.k : act_of(P, c0, act_block(P, h0));
+        val1 = P.ace ? P.k : act_of(P, c0, act_block(P, h1));
+        const uint32_t q0 = h0 / F, q1 = h1 / F;
+        const uint32_t sh0 = (h0 - q0 * F) * WB, sh1 = (h1 - q1 * F) * WB;
         uint32_t *a0[RM], *a1[RM];
         uint32_t o0[RM], o1[RM];
 #pragma unroll
@@ -80,15 +136,17 @@ __global__ void __launch_bounds__(256) ingest_kernel(Params P, uint32_t *pool, c
 #pragma unroll
         for (int i = 0; i < RM; i++) {
             if (i < r) {
-                o0[i] = *a0[i];
-                o1[i] = *a1[i];
+                o0[i] = do0 ? *a0[i] : 0u;
+                o1[i] = do1 ? *a1[i] : 0u;
             }
         }
 #pragma unroll
         for (int i = 0; i < RM; i++) {
             if (i < r) {
-                set_field(a0[i], o0[i], sh0, val0, FM);
-                set_field(a1[i], o1[i], sh1, val1, FM);
+                if (do0)
+                    set_field(a0[i], o0[i], sh0, val0, FM);
+                if (do1)
+                    set_field(a1[i], o1[i], sh1, val1, FM);
             }
         }
     }
@@ -106,28 +164,67 @@ __global__ void __launch_bounds__(256) ingest_kernel(Params P, uint32_t *pool, c
 
 }  // namespace
 
-cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uint32_t *pairs, uint64_t n, uint32_t c0,
-                          int sms, cudaStream_t s, uint64_t *launches)
+cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uint32_t *pairs, uint64_t n,
+                          const unsigned long long *n_dev, const SliceCtl *ctl, int sms, cudaStream_t s,
+                          uint64_t *launches)
 {
-    if (n == 0)
+    if (n == 0 && n_dev == nullptr)
         return cudaSuccess;
     const uint64_t nvec = n / 2;
-    const uint2 *tail = (n & 1) ? reinterpret_cast<const uint2 *>(pairs + 2 * (n - 1)) : nullptr;
-    const uint4 *p4 = reinterpret_cast<const uint4 *>(pairs);
     *launches += 1;
+    const size_t smem = sizeof(unsigned long long) << SEEN_LOG2;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         auto kern = P.r == 4 ? ingest_kernel<WB, 4> : ingest_kernel<WB, 0>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
         static int per_sm[2] = {0, 0};
         int &occ = per_sm[P.r == 4 ? 0 : 1];
         if (occ == 0)
-            occ = resident_blocks(kern, 256, 0);
-        const uint64_t want = (nvec + 255) / 256;
+            occ = resident_blocks(kern, INGEST_THREADS, smem);
+        const uint64_t want = (nvec + INGEST_THREADS - 1) / INGEST_THREADS;
         const uint64_t full = (uint64_t)sms * occ;
-        const unsigned grid = (unsigned)(want < 1 ? 1 : (want < full ? want : full));
-        kern<<<grid, 256, 0, s>>>(P, pool, p4, nvec, tail, c0);
+        // with the count only known on the device, the full resident grid
+        const unsigned grid = (unsigned)(n_dev ? full : (want < 1 ? 1 : (want < full ? want : full)));
+        kern<<<grid, INGEST_THREADS, smem, s>>>(P, pool, pairs, n, n_dev, ctl);
         return cudaGetLastError();
     });
+}
+
+namespace {
+
+__global__ void advance_ctl_kernel(Params P, SliceCtl *ctl)
+{
+    *ctl = slice_ctl(P, ctl->t + 1);
+}
+
+__global__ void reset_kernel(unsigned long long *aat, uint32_t *sa_n, uint32_t nseg, Status *status)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nseg; i += gridDim.x * blockDim.x) {
+        aat[i] = 0;
+        sa_n[i] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *status = Status{};
+}
+
+}  // namespace
+
+cudaError_t launch_advance_ctl(const Params &P, SliceCtl *ctl, cudaStream_t s, uint64_t *launches)
+{
+    *launches += 1;
+    advance_ctl_kernel<<<1, 1, 0, s>>>(P, ctl);
+    return cudaGetLastError();
+}
+
+// Zero the scan outputs that are accumulated with atomics, and the status.
+cudaError_t launch_reset(unsigned long long *aat, uint32_t *sa_n, uint32_t nseg, Status *status, cudaStream_t s,
+                         uint64_t *launches)
+{
+    *launches += 1;
+    reset_kernel<<<(nseg + 255) / 256 < 1 ? 1 : (nseg + 255) / 256, 256, 0, s>>>(aat, sa_n, nseg, status);
+    return cudaGetLastError();
 }
 
 }  // namespace asse

@@ -22,7 +22,9 @@ struct Params {
     uint32_t ace;       // 1: aging counters
     uint32_t nf;        // frames 2^u
     uint32_t mw;        // 32-bit words of one active mask, ceil(g/32)
-    uint64_t blk_magic; // ceil(2^32 / floor(g/2k))
+    uint32_t blk;       // ATs per ACT block: floor(g/2k)
+    uint32_t F;         // fields per 32-bit word: floor(32/w)
+    uint64_t blk_magic; // ceil(2^32 / blk)
     uint64_t Ainv;      // A^-1 mod p (may exceed 2^32)
     uint64_t bh_a, bh_b;
     uint32_t xshift[8]; // 2W - c - s*i: shift of the doubled LBS giving x_i
@@ -34,7 +36,9 @@ struct Status {
     unsigned long long n_report;  // candidates with estimate >= theta
     unsigned long long needed;    // tuples the overflowing join level needed
     unsigned int overflow;        // a frame exceeded the restore capacity
-    unsigned int pad;
+    unsigned int error;           // a device-side wait gave up (bounded mbarrier wait)
+    unsigned int tile_next;       // scan work queue: next tile to hand out
+    unsigned int pad[3];
 };
 
 // A partial or complete column tuple of the restore join.
@@ -52,6 +56,75 @@ struct Refresh {
     uint32_t n_ranges; // 0, 1 or 2 distinct word ranges
 };
 
+// Tile geometry of the scan kernel (asse_scan.cu).
+struct ScanGeom {
+    uint32_t lpa;         // lanes per ATV
+    uint32_t apt;         // ATVs per warp tile (32 / lpa)
+    uint32_t wseg;        // words per lane segment (Wd / lpa)
+    uint32_t seg_stride;  // shared-memory words per lane segment (odd number of 16-byte units)
+    uint32_t tile_words;  // 32 * seg_stride
+    uint32_t warps;       // warps per CTA that stream tiles
+    uint32_t tile_offset; // byte offset of the tile buffers in dynamic shared memory
+    uint32_t smem;        // dynamic shared memory bytes
+};
+ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit);
+
+// Slice-dependent launch arguments, kept in device memory so that a captured
+// CUDA graph replays unchanged from slice to slice: the open slice, the ACT
+// of its block 0, and the words Algorithm 2 checks when the next slice opens.
+struct SliceCtl {
+    unsigned long long t;
+    uint32_t c0;
+    uint32_t pad;
+    Refresh R;
+};
+
+// Words holding the two ACT blocks whose ACT becomes 0 and k when slice
+// t_new opens (blocks are contiguous: the first 2k-1 of blk ATs, the last the
+// rest of g).
+__host__ __device__ inline Refresh refresh_for(uint32_t k, uint32_t g, uint32_t blk, uint32_t F,
+                                               unsigned long long t_new)
+{
+    const uint32_t k2 = 2 * k;
+    Refresh R{};
+    R.c0n = (uint32_t)(t_new % k2);
+    const uint32_t b[2] = {(k2 - R.c0n) % k2, (k + k2 - R.c0n) % k2};
+    uint32_t lo[2], hi[2];
+    for (int i = 0; i < 2; i++) {
+        const uint32_t flo = b[i] * blk, fhi = b[i] == k2 - 1 ? g : (b[i] + 1) * blk;
+        lo[i] = flo / F;
+        hi[i] = (fhi - 1) / F;
+    }
+    if (lo[1] < lo[0]) {
+        const uint32_t a = lo[0], c = hi[0];
+        lo[0] = lo[1];
+        hi[0] = hi[1];
+        lo[1] = a;
+        hi[1] = c;
+    }
+    if (lo[1] <= hi[0] + 1) {
+        R.q_lo[0] = lo[0];
+        R.q_hi[0] = hi[1] > hi[0] ? hi[1] : hi[0];
+        R.n_ranges = 1;
+    } else {
+        R.q_lo[0] = lo[0];
+        R.q_hi[0] = hi[0];
+        R.q_lo[1] = lo[1];
+        R.q_hi[1] = hi[1];
+        R.n_ranges = 2;
+    }
+    return R;
+}
+
+__host__ __device__ inline SliceCtl slice_ctl(const Params &P, unsigned long long t)
+{
+    SliceCtl c{};
+    c.t = t;
+    c.c0 = (uint32_t)(t % P.k2);
+    c.R = refresh_for(P.k, P.g, P.blk, P.F, t + 1);
+    return c;
+}
+
 struct ScanOut {
     uint16_t *cnt;
     unsigned long long *aat;
@@ -61,11 +134,17 @@ struct ScanOut {
 
 // Kernel launchers (asse_kernels.cu).  Each returns the cudaError_t of its
 // launch and adds the number of kernels it launched to *launches.
+// n pairs, or (n_dev != null) as many as *n_dev says at run time.
 cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uint32_t *pairs, uint64_t n,
-                          uint32_t c0, int sms, cudaStream_t s, uint64_t *launches);
-cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t c0, uint32_t kp, const Refresh *fuse,
+                          const unsigned long long *n_dev, const SliceCtl *ctl, int sms, cudaStream_t s,
+                          uint64_t *launches);
+// Open the next slice on the device: ctl = slice_ctl(ctl->t + 1).
+cudaError_t launch_advance_ctl(const Params &P, SliceCtl *ctl, cudaStream_t s, uint64_t *launches);
+cudaError_t launch_reset(unsigned long long *aat, uint32_t *sa_n, uint32_t nseg, Status *status, cudaStream_t s,
+                         uint64_t *launches);
+cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
                         const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches);
-cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const Refresh &R, int sms, cudaStream_t s,
+cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const SliceCtl *ctl, int sms, cudaStream_t s,
                            uint64_t *launches);
 cudaError_t launch_restore(const Params &P, const ScanOut &o, Tuple *scratch, uint32_t cap, asse_superpoint *csip,
                            asse_superpoint *report, uint64_t out_cap, cudaStream_t s, uint64_t *launches);
@@ -83,6 +162,38 @@ struct RestoreView {
     uint64_t *launches;
 };
 int pool_restore_view(asse_pool *p, RestoreView *v);
+
+// What asse_features (asse_learn.cu) needs: the live pool state of the open
+// slice and the last scan's window and loads.  ESTATE unless the pool was
+// scanned and neither refreshed nor ingested into since.
+struct FeatureView {
+    Params P;
+    uint32_t w;
+    const uint32_t *pool;
+    uint32_t c0, kp;
+    const unsigned long long *aat;
+    cudaStream_t stream;
+    uint64_t *launches;
+    int sms;
+};
+int pool_feature_view(asse_pool *p, FeatureView *v);
 int pool_fail(asse_pool *p, int code, const std::string &msg);
+
+// Pieces of asse_close_slice / asse_ingest for the server (asse_serve.cu),
+// which captures them into CUDA graphs: enqueue the device work of a close
+// (no host bookkeeping), do the host bookkeeping of one close, and enqueue an
+// ingest whose pair count is read from device memory.
+int pool_enqueue_close(asse_pool *p, uint32_t kp);
+void pool_after_close(asse_pool *p, uint32_t kp);
+int pool_enqueue_ingest(asse_pool *p, const uint32_t *pairs_dev, const unsigned long long *n_dev);
+struct PoolBuffers {
+    Status *status;
+    asse_superpoint *report;
+    uint64_t out_cap;
+    cudaStream_t stream;
+    uint32_t cap;
+};
+PoolBuffers pool_buffers(asse_pool *p);
+uint64_t pool_device_bytes(const asse_config *cfg);
 
 }  // namespace asse

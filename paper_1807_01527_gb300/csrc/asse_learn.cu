@@ -1,0 +1,829 @@
+// Learned per-ATV cardinality model (include/asse_learn.h): feature rows of
+// ATV states, synthetic training states, and the MLP (FEAT -> 256 -> 256 -> 1,
+// ReLU) with its training step, all in the library's own kernels.
+//
+// Matrix products run on the tensor cores through mma.sync m16n8k16 with BF16
+// operands and FP32 accumulation, in one tiled kernel whose operands are
+// addressed by (row, k) strides, so every product of the forward and backward
+// pass (including the transposed ones of the weight gradients, split over
+// the batch) is the same kernel with a different epilogue: bias + ReLU ->
+// BF16, bias + ReLU + dot with w3 (the last layer fused into the second),
+// gradient masked by the ReLU -> BF16, or FP32 atomic accumulation.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/asse_learn.h"
+#include "asse_device.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace asse {
+
+namespace {
+
+constexpr int FEAT = ASSE_FEAT;
+constexpr int HID = ASSE_HID;
+// offsets of the parameter blocks in the flat fp32 parameter vector
+constexpr size_t OFF_W1 = 0;
+constexpr size_t OFF_B1 = OFF_W1 + (size_t)HID * FEAT;
+constexpr size_t OFF_W2 = OFF_B1 + HID;
+constexpr size_t OFF_B2 = OFF_W2 + (size_t)HID * HID;
+constexpr size_t OFF_W3 = OFF_B2 + HID;
+constexpr size_t OFF_B3 = OFF_W3 + HID;
+constexpr size_t NPARAMS = OFF_B3 + 1;
+static_assert(NPARAMS == ASSE_MLP_NPARAMS, "parameter layout");
+
+// ---------------------------------------------------------------- features
+
+// Feature row of one ATV from its packed words (global or shared), computed
+// by one warp: active ATs per age (Algorithm 1 for the latest kp slices) and
+// their total, then the three load features.
+template <int WB>
+__device__ void atv_features(const Params &P, const uint32_t *words, uint32_t c0, uint32_t kp, float lp, float lup,
+                             float lmean, uint32_t *hist, bf16 *row, uint32_t lane, uint32_t *cnt_out)
+{
+    constexpr uint32_t F = 32 / WB;
+    constexpr uint32_t FM = (1u << WB) - 1;
+    for (uint32_t i = lane; i < 64; i += 32)
+        hist[i] = 0;
+    __syncwarp();
+    uint32_t cnt = 0;
+    const uint32_t nw = (P.g + F - 1) / F;
+    for (uint32_t q = lane; q < nw; q += 32) {
+        const uint32_t w = words[q];
+        for (uint32_t j = 0; j < F; j++) {
+            const uint32_t h = q * F + j;
+            if (h >= P.g)
+                break;
+            const uint32_t v = (w >> (j * WB)) & FM;
+            bool active;
+            uint32_t age;
+            if (P.ace) {
+                active = v + kp >= P.k + 1;  // a counter visited age slices ago holds k - age
+                age = P.k - v;
+            } else {
+                uint32_t d = act_of(P, c0, act_block(P, h)) + P.k2 - v;
+                d = d >= P.k2 ? d - P.k2 : d;
+                active = v < P.k2 && d < kp;
+                age = d;
+            }
+            if (active) {
+                cnt++;
+                if (age < 64)
+                    atomicAdd(&hist[age], 1u);
+            }
+        }
+    }
+    cnt = __reduce_add_sync(FULL_MASK, cnt);
+    __syncwarp();
+    const float inv_g = 1.0f / (float)P.g;
+    for (uint32_t e = lane; e < FEAT; e += 32) {
+        float v = 0.0f;
+        if (e == 0)
+            v = (float)cnt * inv_g;
+        else if (e <= 64)
+            v = (float)hist[e - 1] * inv_g;
+        else if (e == 65)
+            v = lp;
+        else if (e == 66)
+            v = lup;
+        else if (e == 67)
+            v = lmean;
+        row[e] = __float2bfloat16_rn(v);
+    }
+    if (cnt_out)
+        *cnt_out = cnt;
+    __syncwarp();
+}
+
+template <int WB>
+__global__ void __launch_bounds__(256) features_kernel(Params P, const uint32_t *pool, uint32_t c0, uint32_t kp,
+                                                       const unsigned long long *aat, bf16 *x, uint32_t total_atv)
+{
+    __shared__ uint32_t hist[8][64];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double denom = (double)P.g * (double)(P.cmask + 1);
+    for (uint32_t atv = blockIdx.x * 8 + warp; atv < total_atv; atv += gridDim.x * 8) {
+        const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
+        double up = 1.0, sum = 0.0, mine = 0.0;
+        for (uint32_t i = 0; i < P.r; i++) {
+            const double pi = (double)aat[(size_t)i * P.nf + frame] / denom;
+            up *= pi;
+            sum += pi;
+            if (i == row)
+                mine = pi;
+        }
+        atv_features<WB>(P, pool + (size_t)atv * P.Wd, c0, kp, (float)mine, (float)up, (float)(sum / P.r),
+                         hist[warp], x + (size_t)atv * FEAT, lane, nullptr);
+    }
+}
+
+// ---------------------------------------------------------------- synthetic states
+
+__device__ __forceinline__ uint64_t splitmix(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ double unit(uint64_t key, uint64_t i)
+{
+    return (double)(splitmix(key ^ splitmix(i)) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+struct SynthArgs {
+    uint64_t seed;
+    uint32_t n_max_log2;
+    float bg_max;
+};
+
+// One block per state: the host's distinct bips and the background set the
+// ATs slice by slice (a later slice overwrites), the state is packed exactly
+// as ingest would have left it at the end of slice k-1, and its feature row
+// is computed from the packed words by atv_features.
+template <int WB>
+__global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint64_t first, uint64_t n, bf16 *x,
+                                                    float *log_n, float *lc)
+{
+    constexpr uint32_t F = 32 / WB;
+    extern __shared__ uint32_t sm[];
+    int16_t *last = reinterpret_cast<int16_t *>(sm);                // [g]
+    uint32_t *words = sm + (P.g + 1) / 2;                           // [Wd]
+    uint32_t *hist = words + P.Wd;                                   // [64]
+    __shared__ uint32_t end[65];
+    __shared__ uint32_t card;
+    __shared__ float pbg;
+    const uint32_t tid = threadIdx.x;
+    for (uint64_t si = blockIdx.x; si < n; si += gridDim.x) {
+        const uint64_t key = splitmix(S.seed ^ splitmix(first + si + 0x51ED270B27ull));
+        if (tid == 0) {
+            const double lnmax = (double)S.n_max_log2 * 0.6931471805599453;
+            double c = floor(exp(unit(key, 1) * lnmax));
+            card = (uint32_t)(c < 1.0 ? 1.0 : c);
+            pbg = (float)(unit(key, 2) * (double)S.bg_max);
+            double tot = 0.0, w[64];
+            for (uint32_t s = 0; s < P.k; s++) {
+                w[s] = -log(unit(key, 16 + s) + 1e-300);
+                tot += w[s];
+            }
+            double cum = 0.0;
+            end[0] = 0;
+            for (uint32_t s = 0; s < P.k; s++) {
+                cum += w[s];
+                end[s + 1] = s + 1 == P.k ? card : (uint32_t)floor((double)card * cum / tot);
+            }
+        }
+        for (uint32_t h = tid; h < P.g; h += blockDim.x)
+            last[h] = -1;
+        __syncthreads();
+        const uint32_t base = (uint32_t)(key >> 32);
+        for (uint32_t s = 0; s < P.k; s++) {
+            for (uint32_t h = tid; h < P.g; h += blockDim.x)
+                if (unit(key ^ 0xB5ull, ((uint64_t)s << 32) | h) < (double)pbg)
+                    last[h] = (int16_t)s;
+            for (uint32_t j = end[s] + tid; j < end[s + 1]; j += blockDim.x)
+                last[bip_hash(P, mix32(base + j))] = (int16_t)s;
+            __syncthreads();
+        }
+        // pack: an AT last set in slice s holds that slice's ACT (C0 = s)
+        for (uint32_t q = tid; q < P.Wd; q += blockDim.x) {
+            uint32_t wd = 0;
+            for (uint32_t j = 0; j < F; j++) {
+                const uint32_t h = q * F + j;
+                if (h < P.g) {
+                    const int s = last[h];
+                    const uint32_t v = s < 0 ? P.k2 : act_of(P, (uint32_t)s, act_block(P, h));
+                    wd |= v << (j * WB);
+                }
+            }
+            words[q] = wd;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            const float pw = 1.0f - powf(1.0f - pbg, (float)P.k);  // background activity over the window
+            uint32_t cnt = 0;
+            atv_features<WB>(P, words, (P.k - 1) % P.k2, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
+                             tid, &cnt);
+            if (tid == 0) {
+                log_n[si] = (float)log((double)card);
+                const double c = cnt >= P.g ? (double)P.g - 0.5 : (double)cnt;
+                lc[si] = (float)(-(double)P.g * log(((double)P.g - c) / (double)P.g));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- GEMM
+
+// Operand addressed by strides: element (i, kk) at p[i * si + kk * sk].
+struct Operand {
+    const bf16 *p;
+    long si, sk;
+};
+
+__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// out = bf16(relu(v + bias[n]))
+struct EpiBiasRelu {
+    const float *bias;
+    bf16 *out;
+    int ld;
+    static constexpr bool kRowDot = false;
+    __device__ void operator()(int m, int n, float v) const
+    {
+        out[(long)m * ld + n] = __float2bfloat16_rn(fmaxf(v + bias[n], 0.0f));
+    }
+};
+
+// h = bf16(relu(v + bias[n])) stored, and y[m] += h * w3[n]
+struct EpiBiasReluDot {
+    const float *bias;
+    const float *w3;
+    bf16 *out;  // may be null (inference)
+    int ld;
+    float *y;
+    static constexpr bool kRowDot = true;
+    __device__ float operator()(int m, int n, float v) const
+    {
+        const bf16 h = __float2bfloat16_rn(fmaxf(v + bias[n], 0.0f));
+        if (out)
+            out[(long)m * ld + n] = h;
+        return __bfloat162float(h) * w3[n];
+    }
+};
+
+// out = bf16(v) where the forward activation was positive, else 0
+struct EpiReluGrad {
+    const bf16 *act;
+    bf16 *out;
+    int ld;
+    static constexpr bool kRowDot = false;
+    __device__ void operator()(int m, int n, float v) const
+    {
+        const float a = __bfloat162float(act[(long)m * ld + n]);
+        out[(long)m * ld + n] = __float2bfloat16_rn(a > 0.0f ? v : 0.0f);
+    }
+};
+
+// out[m][n] += v (split over the reduction dimension)
+struct EpiAtomic {
+    float *out;
+    int ld;
+    static constexpr bool kRowDot = false;
+    __device__ void operator()(int m, int n, float v) const { atomicAdd(&out[(long)m * ld + n], v); }
+};
+
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+// C[M][N] = sum_k A(m, k) B(n, k); blockIdx.z takes the k range
+// [z * kchunk, (z+1) * kchunk).  4 warps, each a 32 x 32 block of the 64 x 64
+// tile as 2 x 4 m16n8k16 products per 16-wide k step.
+template <class Epi>
+__global__ void __launch_bounds__(128) gemm_kernel(Operand A, Operand B, int M, int N, int K, int kchunk, Epi epi)
+{
+    __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
+    __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                acc[i][j][e] = 0.0f;
+    const bool a_kfast = A.sk == 1, b_kfast = B.sk == 1;
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
+        for (int e = tid; e < GBM * GBK; e += 128) {
+            const int r = a_kfast ? e / GBK : e % GBM, c = a_kfast ? e % GBK : e / GBM;
+            const int m = m0 + r, k = k0 + c;
+            As[r][c] = (m < M && k < ke) ? A.p[(long)m * A.si + (long)k * A.sk] : __float2bfloat16_rn(0.0f);
+        }
+        for (int e = tid; e < GBN * GBK; e += 128) {
+            const int r = b_kfast ? e / GBK : e % GBN, c = b_kfast ? e % GBK : e / GBN;
+            const int n = n0 + r, k = k0 + c;
+            Bs[r][c] = (n < N && k < ke) ? B.p[(long)n * B.si + (long)k * B.sk] : __float2bfloat16_rn(0.0f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = wm * 32 + i * 16 + g;
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int r = wn * 32 + j * 8 + g;
+                bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + 2 * t]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    // element e of acc[i][j]: row g (+8 for e >= 2), column 2t + (e & 1)
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int m = m0 + wm * 32 + i * 16 + g + 8 * h;
+            float dot = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int n = n0 + wn * 32 + j * 8 + 2 * t + e;
+                    if (m < M && n < N) {
+                        if constexpr (Epi::kRowDot)
+                            dot += epi(m, n, acc[i][j][2 * h + e]);
+                        else
+                            epi(m, n, acc[i][j][2 * h + e]);
+                    }
+                }
+            }
+            if constexpr (Epi::kRowDot) {
+                // the four threads of a row hold its 32 columns of this warp
+                dot += __shfl_xor_sync(FULL_MASK, dot, 1);
+                dot += __shfl_xor_sync(FULL_MASK, dot, 2);
+                if (t == 0 && m < M)
+                    atomicAdd(&epi.y[m], dot);
+            }
+        }
+    }
+}
+
+template <class Epi>
+cudaError_t gemm(Operand A, Operand B, int M, int N, int K, int splits, Epi epi, cudaStream_t s, uint64_t *launches)
+{
+    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    const dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, (K + kchunk - 1) / kchunk);
+    *launches += 1;
+    gemm_kernel<Epi><<<grid, 128, 0, s>>>(A, B, M, N, K, kchunk, epi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- elementwise
+
+__global__ void fill_kernel(float *y, uint64_t n, const float *value)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        y[i] = *value;
+}
+
+// dy = 2 (y - t) / n, loss += (y - t)^2 / n
+__global__ void loss_kernel(const float *y, const float *t, uint64_t n, float *dy, float *loss)
+{
+    float acc = 0.0f;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        dy[i] = 2.0f * d / (float)n;
+        acc += d * d / (float)n;
+    }
+    acc += __shfl_xor_sync(FULL_MASK, acc, 16);
+    acc += __shfl_xor_sync(FULL_MASK, acc, 8);
+    acc += __shfl_xor_sync(FULL_MASK, acc, 4);
+    acc += __shfl_xor_sync(FULL_MASK, acc, 2);
+    acc += __shfl_xor_sync(FULL_MASK, acc, 1);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(loss, acc);
+}
+
+// dZ2 = bf16(dy[m] w3[n] [H2 > 0]); dw3[n] += dy[m] H2[m][n]; db2[n] += dZ2;
+// db3 += dy.  One block of HID threads per chunk of rows.
+__global__ void __launch_bounds__(HID) out_grad_kernel(const float *dy, const bf16 *H2, const float *w3, uint64_t n,
+                                                       bf16 *dZ2, float *g_w3, float *g_b2, float *g_b3)
+{
+    const int col = threadIdx.x;
+    float sw = 0.0f, sb = 0.0f, s3 = 0.0f;
+    for (uint64_t m = blockIdx.x; m < n; m += gridDim.x) {
+        const float d = dy[m];
+        const float h = __bfloat162float(H2[m * HID + col]);
+        const bf16 z = __float2bfloat16_rn(h > 0.0f ? d * w3[col] : 0.0f);
+        dZ2[m * HID + col] = z;
+        sw += d * h;
+        sb += __bfloat162float(z);
+        if (col == 0)
+            s3 += d;
+    }
+    atomicAdd(&g_w3[col], sw);
+    atomicAdd(&g_b2[col], sb);
+    if (col == 0)
+        atomicAdd(g_b3, s3);
+}
+
+// g_b[n] += sum over rows of Z[m][n]
+__global__ void __launch_bounds__(HID) colsum_kernel(const bf16 *Z, uint64_t n, float *g_b)
+{
+    const int col = threadIdx.x;
+    float s = 0.0f;
+    for (uint64_t m = blockIdx.x; m < n; m += gridDim.x)
+        s += __bfloat162float(Z[m * HID + col]);
+    atomicAdd(&g_b[col], s);
+}
+
+// Adam on the fp32 parameters, refreshing the bf16 copies of W1 and W2.
+__global__ void adam_kernel(float *p, const float *gr, float *m1, float *m2, uint64_t n, float lr, float b1t,
+                            float b2t, bf16 *w1b, bf16 *w2b)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float g = gr[i];
+        const float a = 0.9f * m1[i] + 0.1f * g;
+        const float b = 0.999f * m2[i] + 0.001f * g * g;
+        m1[i] = a;
+        m2[i] = b;
+        const float v = p[i] - lr * (a / b1t) / (sqrtf(b / b2t) + 1e-8f);
+        p[i] = v;
+        if (i < OFF_B1)
+            w1b[i - OFF_W1] = __float2bfloat16_rn(v);
+        else if (i >= OFF_W2 && i < OFF_B2)
+            w2b[i - OFF_W2] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void to_bf16_kernel(const float *p, bf16 *w1b, bf16 *w2b)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < NPARAMS;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (i < OFF_B1)
+            w1b[i - OFF_W1] = __float2bfloat16_rn(p[i]);
+        else if (i >= OFF_W2 && i < OFF_B2)
+            w2b[i - OFF_W2] = __float2bfloat16_rn(p[i]);
+    }
+}
+
+uint32_t ceil_log2_host(uint32_t v)
+{
+    uint32_t b = 0;
+    while ((1u << b) < v)
+        b++;
+    return b;
+}
+
+}  // namespace
+
+}  // namespace asse
+
+using namespace asse;
+
+struct asse_mlp {
+    cudaStream_t stream = nullptr;
+    float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
+    bf16 *w1b = nullptr, *w2b = nullptr;
+    uint64_t cap = 0;  // rows of the activation workspace
+    bf16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    float *y = nullptr, *dy = nullptr, *loss = nullptr;
+    uint64_t steps = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int mlp_fail(asse_mlp *m, int code, const std::string &msg)
+{
+    if (m)
+        m->err = msg;
+    return code;
+}
+
+#define MCK(m, call)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return mlp_fail((m), ASSE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure_workspace(asse_mlp *m, uint64_t rows)
+{
+    if (rows <= m->cap)
+        return ASSE_OK;
+    cudaStreamSynchronize(m->stream);
+    cudaFree(m->H1);
+    cudaFree(m->H2);
+    cudaFree(m->dZ2);
+    cudaFree(m->dZ1);
+    cudaFree(m->y);
+    cudaFree(m->dy);
+    m->H1 = m->H2 = m->dZ2 = m->dZ1 = nullptr;
+    m->y = m->dy = nullptr;
+    m->cap = 0;
+    const size_t act = rows * HID * sizeof(bf16);
+    MCK(m, cudaMalloc(&m->H1, act));
+    MCK(m, cudaMalloc(&m->H2, act));
+    MCK(m, cudaMalloc(&m->dZ2, act));
+    MCK(m, cudaMalloc(&m->dZ1, act));
+    MCK(m, cudaMalloc(&m->y, rows * sizeof(float)));
+    MCK(m, cudaMalloc(&m->dy, rows * sizeof(float)));
+    m->cap = rows;
+    return ASSE_OK;
+}
+
+// Forward pass of n rows into y (and H1, H2 kept for the backward pass).
+int forward(asse_mlp *m, const bf16 *x, uint64_t n, float *y, bool keep)
+{
+    const float *P = m->params;
+    MCK(m, cudaGetLastError());
+    fill_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, m->stream>>>(y, n, P + OFF_B3);
+    m->launches++;
+    MCK(m, gemm(Operand{x, FEAT, 1}, Operand{m->w1b, FEAT, 1}, (int)n, HID, FEAT, 1,
+                EpiBiasRelu{P + OFF_B1, m->H1, HID}, m->stream, &m->launches));
+    MCK(m, gemm(Operand{m->H1, HID, 1}, Operand{m->w2b, HID, 1}, (int)n, HID, HID, 1,
+                EpiBiasReluDot{P + OFF_B2, P + OFF_W3, keep ? m->H2 : nullptr, HID, y}, m->stream, &m->launches));
+    return ASSE_OK;
+}
+
+int backward(asse_mlp *m, const bf16 *x, const float *t, uint64_t n, float *loss_dev)
+{
+    if (int rc = ensure_workspace(m, n))
+        return rc;
+    if (int rc = forward(m, x, n, m->y, true))
+        return rc;
+    float *G = m->grads;
+    MCK(m, cudaMemsetAsync(G, 0, NPARAMS * sizeof(float), m->stream));
+    MCK(m, cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
+    const unsigned eb = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    loss_kernel<<<eb, 256, 0, m->stream>>>(m->y, t, n, m->dy, m->loss);
+    const unsigned rb = (unsigned)(n < 2048 ? n : 2048);
+    out_grad_kernel<<<rb, HID, 0, m->stream>>>(m->dy, m->H2, m->params + OFF_W3, n, m->dZ2, G + OFF_W3, G + OFF_B2,
+                                              G + OFF_B3);
+    m->launches += 2;
+    MCK(m, cudaGetLastError());
+    const int splits = (int)((n + 1023) / 1024);
+    // dW2[o][i] = sum_m dZ2[m][o] H1[m][i]
+    MCK(m, gemm(Operand{m->dZ2, 1, HID}, Operand{m->H1, 1, HID}, HID, HID, (int)n, splits,
+                EpiAtomic{G + OFF_W2, HID}, m->stream, &m->launches));
+    // dZ1 = (dZ2 W2) masked by H1 > 0
+    MCK(m, gemm(Operand{m->dZ2, HID, 1}, Operand{m->w2b, 1, HID}, (int)n, HID, HID, 1,
+                EpiReluGrad{m->H1, m->dZ1, HID}, m->stream, &m->launches));
+    colsum_kernel<<<rb, HID, 0, m->stream>>>(m->dZ1, n, G + OFF_B1);
+    m->launches++;
+    // dW1[o][j] = sum_m dZ1[m][o] X[m][j]
+    MCK(m, gemm(Operand{m->dZ1, 1, HID}, Operand{x, 1, FEAT}, HID, FEAT, (int)n, splits,
+                EpiAtomic{G + OFF_W1, FEAT}, m->stream, &m->launches));
+    if (loss_dev)
+        MCK(m, cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+    return ASSE_OK;
+}
+
+template <typename Fn>
+cudaError_t dispatch_w_host(uint32_t w, Fn &&fn)
+{
+    return dispatch_w(w, fn);
+}
+
+}  // namespace
+
+extern "C" {
+
+int asse_features(asse_pool *pool, uint16_t *x_dev)
+{
+    if (!pool || !x_dev)
+        return pool ? pool_fail(pool, ASSE_EINVAL, "x_dev is NULL") : ASSE_EINVAL;
+    FeatureView v;
+    if (int rc = pool_feature_view(pool, &v))
+        return rc;
+    if (v.kp > 64)
+        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
+    const uint32_t total = v.P.r << v.P.E_log2;
+    cudaError_t e = dispatch_w(v.w, [&](auto wb) {
+        constexpr int WB = decltype(wb)::value;
+        const unsigned grid = (unsigned)v.sms * 8;
+        features_kernel<WB><<<grid, 256, 0, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
+                                                         reinterpret_cast<bf16 *>(x_dev), total);
+        return cudaGetLastError();
+    });
+    *v.launches += 1;
+    if (e != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, std::string("features launch: ") + cudaGetErrorString(e));
+    return ASSE_OK;
+}
+
+int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uint16_t *x_dev, float *log_n_dev,
+                      float *lc_dev, void *stream)
+{
+    if (!cfg || (n > 0 && (!x_dev || !log_n_dev || !lc_dev)))
+        return ASSE_EINVAL;
+    if (cfg->k < 1 || cfg->k > 64 || cfg->g < 2 * cfg->k || cfg->g > 4096 || cfg->r < 1 || cfg->n_max_log2 > 24 ||
+        (cfg->bh_a & 1) == 0 || !(cfg->bg_max >= 0.0f && cfg->bg_max <= 1.0f))
+        return ASSE_EINVAL;
+    if (n == 0)
+        return ASSE_OK;
+    Params P{};
+    P.k = cfg->k;
+    P.k2 = 2 * cfg->k;
+    P.g = cfg->g;
+    P.r = cfg->r;
+    P.blk = cfg->g / (2 * cfg->k);
+    P.blk_magic = ((1ull << 32) + P.blk - 1) / P.blk;
+    P.bh_a = cfg->bh_a;
+    P.bh_b = cfg->bh_b;
+    const uint32_t w = ceil_log2_host(2 * cfg->k + 1);
+    const uint32_t Fw = 32 / w;
+    P.Wd = ((cfg->g + Fw - 1) / Fw + 7) / 8 * 8;
+    SynthArgs S{cfg->seed, cfg->n_max_log2, cfg->bg_max};
+    const size_t smem = ((cfg->g + 1) / 2 + P.Wd + 64) * sizeof(uint32_t);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(n < (uint64_t)sms * 8 ? n : (uint64_t)sms * 8);
+    cudaError_t e = dispatch_w(w, [&](auto wb) {
+        constexpr int WB = decltype(wb)::value;
+        synth_kernel<WB><<<grid, 256, smem, (cudaStream_t)stream>>>(P, S, first, n, reinterpret_cast<bf16 *>(x_dev),
+                                                                   log_n_dev, lc_dev);
+        return cudaGetLastError();
+    });
+    return e == cudaSuccess ? ASSE_OK : ASSE_ECUDA;
+}
+
+int asse_mlp_create(uint64_t seed, void *stream, asse_mlp **out)
+{
+    if (!out)
+        return ASSE_EINVAL;
+    *out = nullptr;
+    asse_mlp *m = new (std::nothrow) asse_mlp();
+    if (!m)
+        return ASSE_ENOMEM;
+    m->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t b) {
+        if (e == cudaSuccess)
+            e = cudaMalloc(p, b);
+    };
+    alloc((void **)&m->params, NPARAMS * sizeof(float));
+    alloc((void **)&m->grads, NPARAMS * sizeof(float));
+    alloc((void **)&m->m1, NPARAMS * sizeof(float));
+    alloc((void **)&m->m2, NPARAMS * sizeof(float));
+    alloc((void **)&m->w1b, (size_t)HID * FEAT * sizeof(bf16));
+    alloc((void **)&m->w2b, (size_t)HID * HID * sizeof(bf16));
+    alloc((void **)&m->loss, sizeof(float));
+    if (e != cudaSuccess) {
+        asse_mlp_destroy(m);
+        return e == cudaErrorMemoryAllocation ? ASSE_ENOMEM : ASSE_ECUDA;
+    }
+    // Kaiming-uniform weights (bound sqrt(6 / fan_in)), zero biases, drawn on
+    // the host from SplitMix64 of the seed
+    std::vector<float> h(NPARAMS, 0.0f);
+    uint64_t state = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto next = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    const double b1 = std::sqrt(6.0 / 68.0), b2 = std::sqrt(6.0 / HID), b3 = std::sqrt(6.0 / HID);
+    for (size_t o = 0; o < (size_t)HID; o++)
+        for (size_t j = 0; j < (size_t)FEAT; j++)
+            h[OFF_W1 + o * FEAT + j] = j < 68 ? (float)((2 * next() - 1) * b1) : 0.0f;
+    for (size_t i = 0; i < (size_t)HID * HID; i++)
+        h[OFF_W2 + i] = (float)((2 * next() - 1) * b2);
+    for (size_t i = 0; i < (size_t)HID; i++)
+        h[OFF_W3 + i] = (float)((2 * next() - 1) * b3);
+    int rc = asse_mlp_set_params(m, h.data());
+    if (rc == ASSE_OK) {
+        cudaMemsetAsync(m->m1, 0, NPARAMS * sizeof(float), m->stream);
+        cudaMemsetAsync(m->m2, 0, NPARAMS * sizeof(float), m->stream);
+        if (cudaStreamSynchronize(m->stream) != cudaSuccess)
+            rc = ASSE_ECUDA;
+    }
+    if (rc != ASSE_OK) {
+        asse_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return ASSE_OK;
+}
+
+void asse_mlp_destroy(asse_mlp *m)
+{
+    if (!m)
+        return;
+    cudaStreamSynchronize(m->stream);
+    for (void *p : {(void *)m->params, (void *)m->grads, (void *)m->m1, (void *)m->m2, (void *)m->w1b, (void *)m->w2b,
+                    (void *)m->H1, (void *)m->H2, (void *)m->dZ2, (void *)m->dZ1, (void *)m->y, (void *)m->dy,
+                    (void *)m->loss})
+        cudaFree(p);
+    delete m;
+}
+
+int asse_mlp_set_stream(asse_mlp *m, void *stream)
+{
+    if (!m)
+        return ASSE_EINVAL;
+    m->stream = (cudaStream_t)stream;
+    return ASSE_OK;
+}
+
+int asse_mlp_get_params(asse_mlp *m, float *host)
+{
+    if (!m || !host)
+        return ASSE_EINVAL;
+    MCK(m, cudaMemcpyAsync(host, m->params, NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    MCK(m, cudaStreamSynchronize(m->stream));
+    return ASSE_OK;
+}
+
+int asse_mlp_set_params(asse_mlp *m, const float *host)
+{
+    if (!m || !host)
+        return ASSE_EINVAL;
+    MCK(m, cudaMemcpyAsync(m->params, host, NPARAMS * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    to_bf16_kernel<<<64, 256, 0, m->stream>>>(m->params, m->w1b, m->w2b);
+    m->launches++;
+    MCK(m, cudaGetLastError());
+    MCK(m, cudaStreamSynchronize(m->stream));
+    return ASSE_OK;
+}
+
+int asse_mlp_get_grads(asse_mlp *m, float *host)
+{
+    if (!m || !host)
+        return ASSE_EINVAL;
+    MCK(m, cudaMemcpyAsync(host, m->grads, NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    MCK(m, cudaStreamSynchronize(m->stream));
+    return ASSE_OK;
+}
+
+int asse_mlp_forward(asse_mlp *m, const uint16_t *x_dev, uint64_t n, float *y_dev)
+{
+    if (!m || (n > 0 && (!x_dev || !y_dev)))
+        return ASSE_EINVAL;
+    if (n > 0x7fffffffull)
+        return mlp_fail(m, ASSE_EINVAL, "at most 2^31-1 rows per call");
+    if (n == 0)
+        return ASSE_OK;
+    if (int rc = ensure_workspace(m, n < 65536 ? n : 65536))
+        return rc;
+    for (uint64_t off = 0; off < n; off += m->cap) {
+        const uint64_t c = n - off < m->cap ? n - off : m->cap;
+        if (int rc = forward(m, reinterpret_cast<const bf16 *>(x_dev) + off * FEAT, c, y_dev + off, false))
+            return rc;
+    }
+    return ASSE_OK;
+}
+
+int asse_mlp_backward(asse_mlp *m, const uint16_t *x_dev, const float *t_dev, uint64_t n, float *loss_dev)
+{
+    if (!m || n == 0 || !x_dev || !t_dev)
+        return ASSE_EINVAL;
+    if (n > 0x7fffffffull)
+        return mlp_fail(m, ASSE_EINVAL, "at most 2^31-1 rows per call");
+    return backward(m, reinterpret_cast<const bf16 *>(x_dev), t_dev, n, loss_dev);
+}
+
+int asse_mlp_train_step(asse_mlp *m, const uint16_t *x_dev, const float *t_dev, uint64_t n, float lr,
+                        float *loss_dev)
+{
+    if (int rc = asse_mlp_backward(m, x_dev, t_dev, n, loss_dev))
+        return rc;
+    m->steps++;
+    const float b1t = 1.0f - powf(0.9f, (float)m->steps), b2t = 1.0f - powf(0.999f, (float)m->steps);
+    adam_kernel<<<128, 256, 0, m->stream>>>(m->params, m->grads, m->m1, m->m2, NPARAMS, lr, b1t, b2t, m->w1b,
+                                           m->w2b);
+    m->launches++;
+    MCK(m, cudaGetLastError());
+    return ASSE_OK;
+}
+
+const char *asse_mlp_last_error(const asse_mlp *m) { return m ? m->err.c_str() : ""; }
+
+}  // extern "C"

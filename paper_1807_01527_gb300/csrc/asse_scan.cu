@@ -1,16 +1,31 @@
 // K2: the per-slice scan of the whole pool, with the refresh fused in, and
 // the standalone refresh kernels.
 //
-// scan_kernel streams the pool in tiles of TA whole ATVs (at most 1024 words,
-// one 128-bit load per thread, the next tile prefetched while this one is
-// processed).  Per ATV it forms |ATV|^{k'} (Algorithm 1 on every field,
-// Sec. 3) by shared-memory sums, adds it to the row-frame load |AAT(k',i,j)|
-// (Sec. 4.3) through a warp-segmented reduction, and for super ATVs (count
-// >= ceil(g - g e^{-theta/g}), Sec. 4.2) records the column index and the
-// g-bit active mask that the restore intersects.  With FUSE, each thread then
-// applies Algorithm 2 for the next slice to its words of the two refreshed ACT
-// blocks (or the per-slice decrement of aging counters) and writes back the
-// words that changed, so the refresh costs no extra read of the pool.
+// scan_kernel is a persistent kernel (one CTA per SM).  Every warp streams
+// tiles of whole ATVs from global memory into shared memory with bulk async
+// copies (cp.async.bulk, completion on an mbarrier, two buffers per warp so the
+// next tile is in flight while this one is processed).  Inside a tile one lane
+// owns one ATV, or a 1/2, 1/4, 1/8 segment of a wide ATV; segments sit in
+// shared memory at a stride of an odd number of 16-byte units, so the lanes'
+// 128-bit reads never conflict.  All lanes walk the same word position at the
+// same time, so the per-position constants are warp-uniform.
+//
+// Activity test (Algorithm 1 on every field of a word at once): the active
+// values of a block form the cyclic window act-k'+1 .. act (mod 2k), i.e. at
+// most two plain ranges.  The even and the odd fields of a word are tested
+// separately, each field then having w free bits above it; with a guard bit
+// just above each field, (v | guard) - lo keeps the guard iff v >= lo and
+// (hi | guard) - v keeps it iff v <= hi, with no borrow between fields.  The
+// per-position constants carry each field's own range, so words that straddle
+// two ACT blocks and the fields past g (empty ranges) need no special case.
+// The refresh (Algorithm 2: values 0..k at new ACT 0; value 0 and k..2k-1 at
+// new ACT k) uses the same range machinery to find the fields to clear.
+//
+// Per ATV the lanes form |ATV|^{k'} (Sec. 3), the row-frame loads |AAT(k',i,j)|
+// (Sec. 4.3) and, for a super ATV (Sec. 4.2), its column and g-bit active
+// mask.  With FUSE the refreshed words (AT) are written back at once, or for
+// aging counters every word is decremented in shared memory and each segment
+// is stored back with a bulk copy.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,8 +36,443 @@ namespace asse {
 
 namespace {
 
-constexpr uint32_t NO_SLOT = 0xffffffffu;
-constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_WARPS = SCAN_THREADS / 32;
+constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz before a wait gives up
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase with the given parity to complete; false if it did not
+// complete within WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES)
+            return false;
+    return true;
+}
+
+// Global -> shared bulk copy completing on an mbarrier (16-byte aligned, size
+// a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Shared -> global bulk copy in this thread's bulk group.
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Until this thread's bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_store_drain()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) accesses of the same memory.
+__device__ __forceinline__ void fence_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- SWAR tests
+
+// Layout of the even/odd field groups of a word of WB-bit fields.
+template <int WB>
+struct Swar {
+    static constexpr uint32_t F = 32 / WB;
+    static constexpr uint32_t FM = (1u << WB) - 1;
+    // position of field j inside its group (the odd group is shifted down by WB)
+    static __host__ __device__ constexpr uint32_t pos(uint32_t j) { return (j >> 1) * 2 * WB; }
+    static __host__ __device__ constexpr uint32_t group_fields(uint32_t odd)
+    {
+        uint32_t m = 0;
+        for (uint32_t j = odd; j < F; j += 2)
+            m |= FM << pos(j);
+        return m;
+    }
+    static __host__ __device__ constexpr uint32_t group_guards(uint32_t odd)
+    {
+        uint32_t m = 0;
+        for (uint32_t j = odd; j < F; j += 2)
+            m |= 1u << (pos(j) + WB);
+        return m;
+    }
+    static __host__ __device__ constexpr uint32_t group_ones(uint32_t odd)
+    {
+        uint32_t m = 0;
+        for (uint32_t j = odd; j < F; j += 2)
+            m |= 1u << pos(j);
+        return m;
+    }
+    static constexpr uint32_t ME = group_fields(0);
+    static constexpr uint32_t HE = group_guards(0);
+    static constexpr uint32_t HO = group_guards(1);
+};
+
+// Per word position: for the even (e) and odd (o) field groups, the low ends
+// lo and the high ends with guards hih = hi | guard of two value ranges.
+struct RangeDesc {
+    uint32_t lo1e, hih1e, lo1o, hih1o, lo2e, hih2e, lo2o, hih2o;
+};
+
+template <int WB>
+__device__ __forceinline__ void put_range(RangeDesc &d, uint32_t j, uint32_t l1, uint32_t h1, uint32_t l2, uint32_t h2)
+{
+    using S = Swar<WB>;
+    const uint32_t p = S::pos(j), g = 1u << (p + WB);
+    if (j & 1) {
+        d.lo1o |= l1 << p;
+        d.hih1o |= (h1 << p) | g;
+        d.lo2o |= l2 << p;
+        d.hih2o |= (h2 << p) | g;
+    } else {
+        d.lo1e |= l1 << p;
+        d.hih1e |= (h1 << p) | g;
+        d.lo2e |= l2 << p;
+        d.hih2e |= (h2 << p) | g;
+    }
+}
+
+// The active-value ranges of every field of word position q.
+template <int WB>
+__device__ RangeDesc count_desc(const Params &P, uint32_t q, uint32_t c0, uint32_t kp)
+{
+    using S = Swar<WB>;
+    RangeDesc d = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t j = 0; j < S::F; j++) {
+        const uint32_t h = q * S::F + j;
+        uint32_t l1 = S::FM, h1 = 0, l2 = S::FM, h2 = 0;  // empty ranges
+        if (h < P.g) {
+            if (P.ace) {
+                l1 = P.k + 1 - kp;
+                h1 = P.k;
+            } else {
+                const uint32_t act = act_of(P, c0, act_block(P, h));
+                if (act + 1 >= kp) {
+                    l1 = act + 1 - kp;
+                    h1 = act;
+                } else {  // the window wraps past 0 to the top of 0..2k-1
+                    l1 = 0;
+                    h1 = act;
+                    l2 = act + P.k2 + 1 - kp;
+                    h2 = P.k2 - 1;
+                }
+            }
+        }
+        put_range<WB>(d, j, l1, h1, l2, h2);
+    }
+    return d;
+}
+
+// The value ranges Algorithm 2 clears in every field of word position q when
+// block 0 has ACT c0n.
+template <int WB>
+__device__ RangeDesc refresh_desc(const Params &P, uint32_t q, uint32_t c0n)
+{
+    using S = Swar<WB>;
+    RangeDesc d = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t j = 0; j < S::F; j++) {
+        const uint32_t h = q * S::F + j;
+        uint32_t l1 = S::FM, h1 = 0, l2 = S::FM, h2 = 0;
+        if (h < P.g && !P.ace) {
+            const uint32_t act = act_of(P, c0n, act_block(P, h));
+            if (act == 0) {
+                l1 = 0;
+                h1 = P.k;
+            } else if (act == P.k) {
+                l1 = P.k;
+                h1 = P.k2 - 1;
+                l2 = 0;
+                h2 = 0;
+            }
+        }
+        put_range<WB>(d, j, l1, h1, l2, h2);
+    }
+    return d;
+}
+
+// Guard bits of the fields of word w whose value lies in one of the ranges.
+template <int WB>
+__device__ __forceinline__ void in_ranges(uint32_t w, const RangeDesc &d, uint32_t &ge_bits, uint32_t &go_bits)
+{
+    using S = Swar<WB>;
+    const uint32_t xe = w & S::ME, xo = (w >> WB) & S::ME;
+    const uint32_t xeh = xe | S::HE, xoh = xo | S::HO;
+    ge_bits = (((xeh - d.lo1e) & (d.hih1e - xe)) | ((xeh - d.lo2e) & (d.hih2e - xe))) & S::HE;
+    go_bits = (((xoh - d.lo1o) & (d.hih1o - xo)) | ((xoh - d.lo2o) & (d.hih2o - xo))) & S::HO;
+}
+
+template <int WB>
+__device__ __forceinline__ uint32_t count_word(uint32_t w, const RangeDesc &d)
+{
+    uint32_t e, o;
+    in_ranges<WB>(w, d, e, o);
+    return __popc(e) + __popc(o);
+}
+
+// Field j (bit j) set iff field j of w is in one of the ranges.
+template <int WB>
+__device__ __forceinline__ uint32_t field_bits(uint32_t w, const RangeDesc &d)
+{
+    using S = Swar<WB>;
+    uint32_t e, o, am = 0;
+    in_ranges<WB>(w, d, e, o);
+#pragma unroll
+    for (uint32_t j = 0; j < S::F; j++)
+        am |= ((((j & 1) ? o : e) >> (S::pos(j) + WB)) & 1u) << j;
+    return am;
+}
+
+// Algorithm 2 on a word: the fields in the refresh ranges become 2k.
+template <int WB>
+__device__ __forceinline__ uint32_t refresh_swar(const Params &P, uint32_t w, const RangeDesc &d)
+{
+    using S = Swar<WB>;
+    uint32_t e, o;
+    in_ranges<WB>(w, d, e, o);
+    const uint32_t fm = ((e >> WB) * S::FM) | (((o >> WB) * S::FM) << WB);
+    uint32_t k2rep = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < S::F; j++)
+        k2rep |= P.k2 << (j * WB);
+    return (w & ~fm) | (k2rep & fm);
+}
+
+// Aging counters: every non-zero field of w loses one.
+template <int WB>
+__device__ __forceinline__ uint32_t decay_swar(uint32_t w)
+{
+    using S = Swar<WB>;
+    const uint32_t xe = w & S::ME, xo = (w >> WB) & S::ME;
+    const uint32_t nz_e = ((xe | S::HE) - S::group_ones(0)) & S::HE;  // guard kept iff the field is >= 1
+    const uint32_t nz_o = ((xo | S::HO) - S::group_ones(1)) & S::HO;
+    return w - (nz_e >> WB) - ((nz_o >> WB) << WB);  // no borrow: each decremented field is >= 1
+}
+
+// ---------------------------------------------------------------- scan kernel
+
+template <int WB, bool FUSE>
+__global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_t *pool, uint32_t kp,
+                                                               const SliceCtl *ctl, ScanOut o, uint32_t total_atv,
+                                                               ScanGeom G)
+{
+    const uint32_t c0 = ctl->c0;
+    const Refresh R = ctl->R;
+    extern __shared__ __align__(128) uint8_t smem[];
+    RangeDesc *cdesc = reinterpret_cast<RangeDesc *>(smem);                 // [Wd]
+    RangeDesc *rdesc = cdesc + P.Wd;                                         // [Wd]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(rdesc + P.Wd);             // [warps][2]
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(mbar + 2 * G.warps);    // [warps][mw]
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(smem + G.tile_offset);    // [warps][2][tile_words]
+
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x) {
+        cdesc[q] = count_desc<WB>(P, q, c0, kp);
+        if (FUSE)
+            rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
+    }
+    if (warp < G.warps && lane == 0) {
+        mbar_init(&mbar[2 * warp], 1);
+        mbar_init(&mbar[2 * warp + 1], 1);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (warp >= G.warps)
+        return;
+
+    const uint32_t a = lane / G.lpa, part = lane - a * G.lpa;  // this lane's ATV in the tile and segment
+    const uint32_t q_first = part * G.wseg;
+    const uint32_t cols = P.cmask + 1;
+    const uint32_t ntiles = (total_atv + G.apt - 1) / G.apt;
+    uint32_t *my_mask = maskbuf + warp * P.mw;
+    uint32_t *tile_buf[2] = {tiles + (2 * warp) * G.tile_words, tiles + (2 * warp + 1) * G.tile_words};
+    uint64_t *bar[2] = {&mbar[2 * warp], &mbar[2 * warp + 1]};
+    uint32_t parity[2] = {0, 0};
+
+    auto issue = [&](uint32_t tile, int b) {
+        const uint32_t atv0 = tile * G.apt;
+        const uint32_t n_atv = min(G.apt, total_atv - atv0);
+        if (lane == 0)
+            mbar_expect_tx(bar[b], n_atv * P.Wd * 4u);
+        __syncwarp();
+        if (a < n_atv)
+            bulk_load(tile_buf[b] + lane * G.seg_stride, pool + (size_t)(atv0 + a) * P.Wd + q_first, G.wseg * 4u,
+                      bar[b]);
+    };
+    // tiles are handed out one at a time from a device-wide counter, so warps
+    // that finish early take more
+    auto grab = [&]() {
+        uint32_t t = 0;
+        if (lane == 0)
+            t = atomicAdd(&o.status->tile_next, 1u);
+        return __shfl_sync(FULL_MASK, t, 0);
+    };
+
+    int b = 0;
+    uint32_t tile = grab();
+    if (tile < ntiles)
+        issue(tile, 0);
+    uint32_t next = tile < ntiles ? grab() : ntiles;
+    if (next < ntiles)
+        issue(next, 1);
+    while (tile < ntiles) {
+        if (!__all_sync(FULL_MASK, mbar_wait(bar[b], parity[b]))) {
+            // the copy did not land: flag it, give the other copy in flight a
+            // bounded chance to finish, and leave
+            if (lane == 0)
+                atomicExch(&o.status->error, 1u);
+            if (next < ntiles)
+                mbar_wait(bar[b ^ 1], parity[b ^ 1]);
+            return;
+        }
+        parity[b] ^= 1;
+        const uint32_t atv0 = tile * G.apt;
+        const uint32_t n_atv = min(G.apt, total_atv - atv0);
+        const bool mine = a < n_atv;
+        uint32_t *row = tile_buf[b] + lane * G.seg_stride;
+        uint32_t cnt = 0;
+        if (mine) {
+#pragma unroll 2
+            for (uint32_t i = 0; i < G.wseg; i += 4) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(row + i);
+                const uint32_t q = q_first + i;
+                cnt += count_word<WB>(x.x, cdesc[q]) + count_word<WB>(x.y, cdesc[q + 1]) +
+                       count_word<WB>(x.z, cdesc[q + 2]) + count_word<WB>(x.w, cdesc[q + 3]);
+            }
+        }
+        for (uint32_t off = 1; off < G.lpa; off <<= 1)
+            cnt += __shfl_xor_sync(FULL_MASK, cnt, off);
+
+        // one lane per ATV: count, row-frame load, super test
+        const uint32_t atv = atv0 + a;
+        const bool head = mine && part == 0;
+        const uint32_t sg = head ? atv >> P.c : 0xffffffffu;  // row * 2^u + frame
+        if (head)
+            o.cnt[atv] = (uint16_t)cnt;
+        {
+            const unsigned grp = __match_any_sync(FULL_MASK, sg);
+            const uint32_t s = __reduce_add_sync(grp, head ? cnt : 0u);
+            if (head && (uint32_t)(__ffs(grp) - 1) == lane && s)
+                atomicAdd(&o.aat[sg], (unsigned long long)s);
+        }
+        const bool sup = head && cnt >= P.T;
+        uint32_t slot = 0;
+        if (sup) {
+            slot = atomicAdd(&o.sa_n[sg], 1u);
+            o.sa_x[(size_t)sg * cols + slot] = atv & P.cmask;
+        }
+        unsigned sbits = __ballot_sync(FULL_MASK, sup);
+        while (sbits) {
+            // the g-bit active mask of one super ATV, for Algorithm 5
+            const uint32_t hl = __ffs(sbits) - 1;
+            sbits &= sbits - 1;
+            const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
+            const uint32_t a_s = hl / G.lpa;
+            const uint32_t sg_a = (atv0 + a_s) >> P.c;
+            for (uint32_t m = lane; m < P.mw; m += 32)
+                my_mask[m] = 0;
+            __syncwarp();
+            if (a == a_s) {
+                constexpr uint32_t F = 32 / WB;
+                for (uint32_t i = 0; i < G.wseg; i++) {
+                    const uint32_t q = q_first + i;
+                    const uint32_t am = field_bits<WB>(row[i], cdesc[q]);
+                    if (am) {
+                        const uint32_t pos = q * F, off = pos & 31;
+                        atomicOr(&my_mask[pos >> 5], am << off);
+                        if (off + F > 32 && (am >> (32 - off)))
+                            atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
+                    }
+                }
+            }
+            __syncwarp();
+            uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
+            for (uint32_t m = lane; m < P.mw; m += 32)
+                dst[m] = my_mask[m];
+            __syncwarp();
+        }
+
+        if (FUSE && !P.ace) {
+            // Algorithm 2 for the next slice on the words of the two refreshed blocks
+            for (uint32_t rr = 0; rr < R.n_ranges; rr++) {
+                const uint32_t lo = max(R.q_lo[rr], q_first), hi = min(R.q_hi[rr] + 1, q_first + G.wseg);
+                if (mine) {
+                    for (uint32_t q = lo; q < hi; q++) {
+                        const uint32_t w = row[q - q_first];
+                        const uint32_t nw = refresh_swar<WB>(P, w, rdesc[q]);
+                        if (nw != w)
+                            pool[(size_t)atv * P.Wd + q] = nw;
+                    }
+                }
+            }
+        }
+        if (FUSE && P.ace) {
+            // every aging counter loses one: decrement in place, store the segment back
+            if (mine) {
+                for (uint32_t i = 0; i < G.wseg; i++)
+                    row[i] = decay_swar<WB>(row[i]);
+                fence_async_smem();
+                bulk_store(pool + (size_t)atv * P.Wd + q_first, row, G.wseg * 4u);
+            }
+        }
+        // this buffer is free again: fetch the tile after next into it
+        __syncwarp();
+        tile = next;
+        next = tile < ntiles ? grab() : ntiles;
+        if (next < ntiles) {
+            if (FUSE && P.ace)
+                bulk_store_drain();  // this buffer's write-back has read its source
+            fence_async_smem();
+            __syncwarp();
+            issue(next, b);
+        }
+        b ^= 1;
+    }
+    if (FUSE && P.ace)
+        bulk_store_drain();
+}
+
+// ---------------------------------------------------------------- A3 alone
 
 // Algorithm 2 on every field of a word whose new ACT is 0 or k.
 template <int WB>
@@ -43,153 +493,11 @@ __device__ __forceinline__ uint32_t refresh_word(const Params &P, uint32_t word,
     return out;
 }
 
-// Aging counters: every non-zero field loses one.
+// One thread per (ATV, word of the two refreshed blocks).
 template <int WB>
-__device__ __forceinline__ uint32_t decay_word(uint32_t word)
+__global__ void __launch_bounds__(256) refresh_kernel(Params P, uint32_t *pool, const SliceCtl *ctl, uint32_t total_atv)
 {
-    constexpr uint32_t F = 32 / WB;
-    constexpr uint32_t FM = (1u << WB) - 1;
-    uint32_t dec = 0;
-#pragma unroll
-    for (uint32_t j = 0; j < F; j++)
-        dec |= (uint32_t)(((word >> (j * WB)) & FM) != 0) << (j * WB);
-    return word - dec;  // no borrow crosses a field: each decremented field is >= 1
-}
-
-__device__ __forceinline__ bool in_refresh(const Refresh &R, uint32_t q)
-{
-    return (R.n_ranges > 0 && q >= R.q_lo[0] && q <= R.q_hi[0]) ||
-           (R.n_ranges > 1 && q >= R.q_lo[1] && q <= R.q_hi[1]);
-}
-
-template <int WB, bool FUSE>
-__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(Params P, uint32_t *pool, uint32_t c0, uint32_t kp,
-                                                            Refresh R, ScanOut o, uint32_t total_atv, uint32_t TA)
-{
-    constexpr uint32_t F = 32 / WB;
-    extern __shared__ uint32_t sm[];
-    uint32_t *cnt_s = sm;           // [TA] active counts
-    uint32_t *slot_s = sm + TA;     // [TA] SA slot of super ATVs
-    uint32_t *mask_s = sm + 2 * TA; // [TA][mw] active masks of super ATVs
-    __shared__ int any_super;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t vpa = P.Wd / 4;            // 128-bit vectors per ATV
-    const uint32_t nv = TA * vpa;             // vectors per tile, <= SCAN_THREADS
-    const uint32_t a_loc = tid / vpa;         // this thread's ATV within the tile
-    const uint32_t q0 = (tid - a_loc * vpa) * 4;
-    const uint32_t ntiles = (total_atv + TA - 1) / TA;
-    const uint32_t cols = P.cmask + 1;
-    const uint32_t mw = P.mw;
-
-    auto load = [&](uint32_t tile) {
-        const uint32_t atv = tile * TA + a_loc;
-        if (tile < ntiles && tid < nv && atv < total_atv)
-            return reinterpret_cast<const uint4 *>(pool + (size_t)atv * P.Wd)[q0 / 4];
-        return make_uint4(0, 0, 0, 0);
-    };
-
-    uint4 next = load(blockIdx.x);
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t atv0 = tile * TA;
-        const uint32_t atv = atv0 + a_loc;
-        const bool mine = tid < nv && atv < total_atv;
-        const uint4 w = next;
-        next = load(tile + gridDim.x);
-        if (tid < TA)
-            cnt_s[tid] = 0;
-        if (tid == 0)
-            any_super = 0;
-        __syncthreads();
-        uint32_t am[4] = {0, 0, 0, 0};
-        if (mine) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const uint32_t q = q0 + e;
-                if (q * F < P.g) {
-                    am[e] = active_fields<WB>(P, u4get(w, e), q, c0, kp);
-                    c += __popc(am[e]);
-                }
-            }
-            if (c)
-                atomicAdd(&cnt_s[a_loc], c);
-        }
-        __syncthreads();
-        {
-            // one thread per ATV of the tile: count, row-frame load, super test
-            const uint32_t a = atv0 + tid;
-            const bool fin = tid < TA && a < total_atv;
-            const unsigned act = __ballot_sync(FULL_MASK, fin);
-            if (fin) {
-                const uint32_t c = cnt_s[tid];
-                o.cnt[a] = (uint16_t)c;
-                const uint32_t sg = a >> P.c;  // row * 2^u + frame
-                const unsigned grp = __match_any_sync(act, sg);
-                const uint32_t sum = __reduce_add_sync(grp, c);
-                if ((uint32_t)(__ffs(grp) - 1) == (tid & 31) && sum)
-                    atomicAdd(&o.aat[sg], (unsigned long long)sum);
-                uint32_t slot = NO_SLOT;
-                if (c >= P.T) {
-                    slot = atomicAdd(&o.sa_n[sg], 1u);
-                    o.sa_x[(size_t)sg * cols + slot] = a & P.cmask;
-                    any_super = 1;
-                }
-                slot_s[tid] = slot;
-            }
-        }
-        __syncthreads();
-        if (any_super) {
-            for (uint32_t i = tid; i < TA * mw; i += SCAN_THREADS)
-                if (slot_s[i / mw] != NO_SLOT)
-                    mask_s[i] = 0;
-            __syncthreads();
-            if (mine && slot_s[a_loc] != NO_SLOT) {
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    if (am[e]) {
-                        const uint32_t pos = (q0 + e) * F, off = pos & 31;
-                        uint32_t *m = mask_s + a_loc * mw + (pos >> 5);
-                        atomicOr(m, am[e] << off);
-                        if (off + F > 32 && (am[e] >> (32 - off)))
-                            atomicOr(m + 1, am[e] >> (32 - off));
-                    }
-                }
-            }
-            __syncthreads();
-            for (uint32_t i = tid; i < TA * mw; i += SCAN_THREADS) {
-                const uint32_t al = i / mw;
-                const uint32_t slot = slot_s[al];
-                if (slot != NO_SLOT) {
-                    const uint32_t sg = (atv0 + al) >> P.c;
-                    o.sa_mask[((size_t)sg * cols + slot) * mw + (i - al * mw)] = mask_s[i];
-                }
-            }
-        }
-        if (FUSE && mine) {
-            uint32_t *wp = pool + (size_t)atv * P.Wd;
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const uint32_t q = q0 + e;
-                if (q * F < P.g) {
-                    const uint32_t word = u4get(w, e);
-                    uint32_t nw = word;
-                    if (P.ace)
-                        nw = decay_word<WB>(word);
-                    else if (in_refresh(R, q))
-                        nw = refresh_word<WB>(P, word, q, R.c0n);
-                    if (nw != word)
-                        wp[q] = nw;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// A3 alone: one thread per (ATV, word of the two refreshed blocks).
-template <int WB>
-__global__ void __launch_bounds__(256) refresh_kernel(Params P, uint32_t *pool, Refresh R, uint32_t total_atv)
-{
+    const Refresh R = ctl->R;
     const uint32_t nw0 = R.n_ranges > 0 ? R.q_hi[0] - R.q_lo[0] + 1 : 0;
     const uint32_t nw1 = R.n_ranges > 1 ? R.q_hi[1] - R.q_lo[1] + 1 : 0;
     const uint64_t nw = nw0 + nw1;
@@ -214,8 +522,8 @@ __global__ void __launch_bounds__(256) ace_decay_kernel(uint4 *pool, uint64_t nv
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
         const uint4 a = pool[v];
-        const uint4 b = make_uint4(decay_word<WB>(a.x), decay_word<WB>(a.y), decay_word<WB>(a.z),
-                                   decay_word<WB>(a.w));
+        const uint4 b = make_uint4(decay_swar<WB>(a.x), decay_swar<WB>(a.y), decay_swar<WB>(a.z),
+                                   decay_swar<WB>(a.w));
         if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w)
             pool[v] = b;
     }
@@ -223,33 +531,56 @@ __global__ void __launch_bounds__(256) ace_decay_kernel(uint4 *pool, uint64_t nv
 
 }  // namespace
 
-uint32_t scan_tile_atvs(uint32_t Wd)
+// Tile geometry of the scan for ATVs of Wd words: lanes per ATV (so a lane
+// holds at most 48 words where Wd allows), the shared-memory stride of a lane's segment (an odd
+// number of 16-byte units) and how many warps fit the shared memory.
+ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit)
 {
-    const uint32_t ta = (SCAN_THREADS * 4) / Wd;
-    return ta < 1 ? 1 : ta;
+    ScanGeom G{};
+    G.lpa = 1;
+    while (Wd / G.lpa > 48 && Wd % (8 * G.lpa) == 0 && G.lpa < 8)
+        G.lpa *= 2;
+    G.wseg = Wd / G.lpa;
+    uint32_t units = G.wseg / 4;
+    if ((units & 1) == 0)
+        units += 1;
+    G.seg_stride = units * 4;
+    G.apt = 32 / G.lpa;
+    G.tile_words = 32 * G.seg_stride;
+    const size_t fixed = (size_t)Wd * 2 * sizeof(RangeDesc);
+    auto head = [&](uint32_t warps) {
+        const size_t h = fixed + 2 * warps * sizeof(uint64_t) + (size_t)warps * mw * 4;
+        return (h + 127) / 128 * 128;
+    };
+    G.warps = SCAN_WARPS;
+    while (G.warps > 1 && head(G.warps) + (size_t)G.warps * 2 * G.tile_words * 4 > smem_limit)
+        G.warps--;
+    G.tile_offset = (uint32_t)head(G.warps);
+    G.smem = G.tile_offset + G.warps * 2 * G.tile_words * 4;
+    return G;
 }
 
-cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t c0, uint32_t kp, const Refresh *fuse,
+cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
                         const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches)
 {
     const uint32_t total = P.r << P.E_log2;
-    const uint32_t TA = scan_tile_atvs(P.Wd);
-    const size_t smem = (size_t)(2 * TA + TA * P.mw) * sizeof(uint32_t);
-    const uint32_t ntiles = (total + TA - 1) / TA;
-    const Refresh R = fuse ? *fuse : Refresh{};
+    const ScanGeom G = scan_geometry(P.Wd, P.mw, 200 * 1024);
+    const uint32_t ntiles = (total + G.apt - 1) / G.apt;
     *launches += 1;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         auto kern = fuse ? scan_kernel<WB, true> : scan_kernel<WB, false>;
-        const int occ = resident_blocks(kern, SCAN_THREADS, smem);
-        const uint64_t full = (uint64_t)sms * occ;
-        const unsigned grid = (unsigned)(ntiles < full ? ntiles : full);
-        kern<<<grid, SCAN_THREADS, smem, s>>>(P, pool, c0, kp, R, o, total, TA);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem);
+        if (e != cudaSuccess)
+            return e;
+        const uint64_t want = (ntiles + G.warps - 1) / G.warps;
+        const unsigned grid = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
+        kern<<<grid, SCAN_THREADS, G.smem, s>>>(P, pool, kp, ctl, o, total, G);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const Refresh &R, int sms, cudaStream_t s,
+cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const SliceCtl *ctl, int sms, cudaStream_t s,
                            uint64_t *launches)
 {
     const uint32_t total = P.r << P.E_log2;
@@ -265,13 +596,11 @@ cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const Re
             return cudaGetLastError();
         });
     }
-    if (R.n_ranges == 0)
-        return cudaSuccess;
     *launches += 1;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         const unsigned grid = (unsigned)sms * resident_blocks(refresh_kernel<WB>, 256, 0);
-        refresh_kernel<WB><<<grid, 256, 0, s>>>(P, pool, R, total);
+        refresh_kernel<WB><<<grid, 256, 0, s>>>(P, pool, ctl, total);
         return cudaGetLastError();
     });
 }

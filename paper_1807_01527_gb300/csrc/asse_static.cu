@@ -13,6 +13,7 @@
 // time.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <mutex>
 #include <string>
 
@@ -77,7 +78,11 @@ extern "C" int asse_restore_static(asse_pool *pool, uint32_t tuples_per_frame, a
         return rc;
     // The scratch is fully written by each frame's join before it is read, so
     // only the counters have to start at zero.
-    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(asse::Status), v.stream);
+    // the caller's counters are the first four 64-bit words of the status the
+    // restore kernel writes; it never touches the fields after them
+    static_assert(offsetof(asse::Status, overflow) + sizeof(unsigned int) <= 4 * sizeof(uint64_t),
+                  "restore counters must fit in 4 x uint64");
+    cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(uint64_t), v.stream);
     if (e != cudaSuccess)
         return asse::pool_fail(pool, ASSE_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     asse::ScanOut o = v.o;

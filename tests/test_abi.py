@@ -54,7 +54,7 @@ def _cfg(**kw):
     (dict(r=1), "r must"), (dict(r=9), "r must"), (dict(c=17), "c <= 16"), (dict(u=9), "u <= 8"),
     (dict(s=0), "s <= c"), (dict(s=13), "s <= c"), (dict(s=3), "completeness"), (dict(A=1), "A must"),
     (dict(bh_a=2), "odd"), (dict(counter=2), "counter"), (dict(theta=0), "theta"),
-    (dict(c=12, u=4, s=10), "s*(r-1) < 32-u"),
+    (dict(c=12, u=4, s=10), "s*(r-1) < 32-u"), (dict(k=100, g=4000), "512 words"),
 ])
 def test_invalid_configs_rejected_without_gpu(lib, bad, msg):
     from paper_1807_01527_gb300 import asse

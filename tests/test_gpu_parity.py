@@ -149,13 +149,16 @@ def test_host_ingest_chunks_and_snapshot(mods):
     p = _params(4, 128, 4, 10, 0, 8, 64, seed=3)
     a = asse.Pool(p, max_batch=1001)
     b = asse.Pool(p)
+    c_pin = asse.Pool(p)
     for t in range(5):
         pairs = mixed_pairs(3, t, 9999, [100, 200])
-        a.ingest(pairs)                  # numpy: host path, 10 chunks
+        a.ingest(pairs)                  # numpy: pageable host memory, staged in 10 chunks
         b.ingest(to_device(pairs))
+        c_pin.ingest(torch.from_numpy(pairs.view(np.int32)).pin_memory())   # pinned: read in place
         np.testing.assert_array_equal(a.read_pool(), b.read_pool())
-        a.close_slice()
-        b.close_slice()
+        np.testing.assert_array_equal(c_pin.read_pool(), b.read_pool())
+        for pl in (a, b, c_pin):
+            pl.close_slice()
     img = a.snapshot()
     c = asse.Pool(p)
     c.load(img)
