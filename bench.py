@@ -104,12 +104,12 @@ class Clocks:
                 "reasons": sorted({n for r in inside for n in r[3]}), "samples": len(inside), "where": where}
 
 
-def oracle_slice_time(w, ingest_sample: int):
+def oracle_slice_time(w, ingest_sample: int, counter: str = "at"):
     """The CPU oracle as it stands (single thread): ingest a sample of one
     slice, then the whole close (counts, loads, restore, NAT + Eq. 4) and the
     refresh.  Returns (seconds per full slice, extrapolated; sample text)."""
     import oracle
-    o = oracle.Oracle.from_params(w.params)
+    o = oracle.Oracle.from_params(w.params, mode=1 if counter == "ace" else 0)
     pairs = w.pairs(0)
     sample = pairs[:ingest_sample]
     t0 = time.perf_counter()
@@ -121,8 +121,8 @@ def oracle_slice_time(w, ingest_sample: int):
     t_close = time.perf_counter() - t0
     per_slice = t_ing * (len(pairs) / len(sample)) + t_close
     text = ("oracle (1 thread): ingest of the first %d pairs of slice 0 timed and scaled to the %d pairs of a "
-            "slice, plus one full close (counts, loads, restore, NAT, Eq. 4) and refresh of the %s pool"
-            % (len(sample), len(pairs), w.name))
+            "slice, plus one full close (counts, loads, restore, NAT, Eq. 4) and refresh of the %s pool (%s counters)"
+            % (len(sample), len(pairs), w.name, counter.upper()))
     return per_slice, text, len(pairs)
 
 
@@ -135,7 +135,7 @@ def run_reference(args, w):
     times = []
     text, n = "", w.n_per_slice
     for i in range(args.warmup + args.steps):
-        per_slice, text, n = oracle_slice_time(w, args.ref_sample)
+        per_slice, text, n = oracle_slice_time(w, args.ref_sample, args.counter)
         if i >= args.warmup:
             times.append(per_slice)
     ms = 1e3 * statistics.mean(times)
@@ -149,6 +149,41 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def _slice_and_distinct(job):
+    """Slice t of a workload and its number of distinct (aip, bip) pairs."""
+    name, seed, t = job
+    p = synth.workload(name, seed=seed).pairs(t)
+    key = (p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64)
+    return p, int(np.unique(key).size)
+
+
+def make_slices(w, n_slices: int):
+    """The first n_slices slices of w, generated in parallel host processes
+    (started with spawn, before any CUDA call of this process)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    jobs = [(w.name, w.seed, t) for t in range(n_slices)]
+    if w.n_per_slice <= (1 << 20):
+        res = [_slice_and_distinct(j) for j in jobs]
+    else:
+        with cf.ProcessPoolExecutor(max_workers=min(n_slices, os.cpu_count() or 1),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_slice_and_distinct, jobs))
+    return [r[0] for r in res], [r[1] for r in res]
+
+
+def reduce_over_ranks(times, counts, device):
+    """Whole-job figures of the replicas: the slowest rank's times (max) and
+    the units all ranks processed (sum)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t] + [float(x) for x in c]
+
+
 def stepwise_breakdown(pool, dev, w, n):
     """Mean device time of each stage of the stepwise close (scan, restore,
     refresh) next to the fused close, over n slices."""
@@ -158,7 +193,7 @@ def stepwise_breakdown(pool, dev, w, n):
     for i in range(n):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record(stream)
-        pool.ingest(dev[i % N_SLICES_CYCLED])
+        pool.ingest(dev[i % len(dev)])
         e[1].record(stream)
         pool.scan(w.k)
         e[2].record(stream)
@@ -171,7 +206,7 @@ def stepwise_breakdown(pool, dev, w, n):
             acc[name].append(e[a].elapsed_time(e[b]))
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        pool.ingest(dev[(i + 1) % N_SLICES_CYCLED])
+        pool.ingest(dev[(i + 1) % len(dev)])
         f0.record(stream)
         pool.close_slice(w.k)
         f1.record(stream)
@@ -310,6 +345,8 @@ def main():
     ap.add_argument("--mode", default="slice", choices=["slice", "serve"],
                     help="slice: one pool, the headline line; serve: the multi-stream serving loop")
     ap.add_argument("--serve-slices", type=int, default=12)
+    ap.add_argument("--counter", default="at", choices=["at", "ace"],
+                    help="at: the paper's asynchronous timestamps; ace: aging counters")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -324,6 +361,12 @@ def main():
         run_reference(args, w)
         return
 
+    # inputs: distinct slices cycled through, resident in HBM (more than L2:
+    # 512 MB for the link workload, about 1 GB for the long one) and the same
+    # slices in pinned host memory
+    n_cycled = N_SLICES_CYCLED if w.n_per_slice <= (8 << 20) else 4
+    host, n_distinct = make_slices(w, n_cycled)
+
     import torch
     from paper_1807_01527_gb300 import asse, build
     torch.cuda.set_device(local)
@@ -335,23 +378,18 @@ def main():
     clocks = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else tempfile.gettempdir(),
                                  "bench_clocks_%d.csv" % rank), local)
 
-    # inputs: N_SLICES_CYCLED distinct slices resident in HBM (512 MB for the
-    # link workload, more than L2) and the same slices in pinned host memory
-    host = [w.pairs(t) for t in range(N_SLICES_CYCLED)]
     dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
     pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host]
     n_pairs = [p.shape[0] for p in host]
     # Algorithm 3 sets r ATs per pair; repeating an identical (aip, bip) pair
     # within a slice changes nothing, so the work a slice requires is the
     # 8-byte read of every pair plus one 32-byte sector for each of the r AT
-    # words of every distinct pair
-    n_distinct = [int(np.unique((p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64)).size)
-                  for p in host]
+    # words of every distinct pair (n_distinct, counted above)
     stream = torch.cuda.current_stream()
-    pool = asse.Pool(w.params, stream=stream.cuda_stream)
+    pool = asse.Pool(w.params, counter=args.counter, stream=stream.cuda_stream)
 
     def step(i, src):
-        pool.ingest(src[i % N_SLICES_CYCLED])
+        pool.ingest(src[i % n_cycled])
         pool.close_slice(w.k)
         return pool.report()
 
@@ -373,7 +411,7 @@ def main():
     pairs_done = 0
     n_reported = 0
     for i in range(args.steps):
-        src = dev[(args.warmup + i) % N_SLICES_CYCLED]
+        src = dev[(args.warmup + i) % n_cycled]
         ev[i][0].record(stream)
         pool.ingest(src)
         ev[i][1].record(stream)
@@ -383,7 +421,7 @@ def main():
         rep = pool.report()
         lat.append(time.perf_counter() - t0)
         n_reported += rep.size
-        pairs_done += n_pairs[(args.warmup + i) % N_SLICES_CYCLED]
+        pairs_done += n_pairs[(args.warmup + i) % n_cycled]
     end.record(stream)
     torch.cuda.synchronize()
     elapsed = start.elapsed_time(end) / 1e3
@@ -402,7 +440,7 @@ def main():
     t0 = time.perf_counter()
     e2e_pairs, d2h = 0, 0
     for i in range(args.steps):
-        j = (args.warmup + i) % N_SLICES_CYCLED
+        j = (args.warmup + i) % n_cycled
         rep = step(j, pinned)
         e2e_pairs += n_pairs[j]
         d2h += rep.nbytes + 32
@@ -412,18 +450,14 @@ def main():
     breakdown = stepwise_breakdown(pool, dev, w, args.warmup) if args.breakdown else None
 
     if world > 1:
-        t = torch.tensor([elapsed, e2e_elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed, e2e_elapsed = float(t[0]), float(t[1])
-        c = torch.tensor([pairs_done, e2e_pairs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        pairs_done, e2e_pairs = float(c[0]), float(c[1])
+        elapsed, e2e_elapsed, pairs_done, e2e_pairs = reduce_over_ranks([elapsed, e2e_elapsed],
+                                                                        [pairs_done, e2e_pairs], "cuda")
 
     if rank == 0:
         ing = statistics.mean(t_ingest)
         cls = statistics.mean(t_close)
         n_avg = statistics.mean(n_pairs)
-        used = [(args.warmup + i) % N_SLICES_CYCLED for i in range(args.steps)]
+        used = [(args.warmup + i) % n_cycled for i in range(args.steps)]
         alg_bytes = statistics.mean(8 * n_pairs[j] + 32 * w.r * n_distinct[j] for j in used)
         peak, peak_src = peaks()
         achieved = alg_bytes / ing / 1e9
@@ -433,16 +467,17 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(workload_desc(w), parallelism="replicas" if world > 1 else "single",
+            "config": dict(workload_desc(w), counter=args.counter.upper(),
+                           parallelism="replicas" if world > 1 else "single",
                            l2="inputs cycle over %d distinct slices (%d MB) held in HBM, more than L2; the pool "
-                              "state stays resident across steps" % (N_SLICES_CYCLED, sum(p.nbytes for p in host) >> 20)),
+                              "state stays resident across steps" % (n_cycled, sum(p.nbytes for p in host) >> 20)),
             "slice_latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                                      int(0.99 * len(lat_ms)))],
                                  "what": "close_slice call to report on the host"},
             "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * cls},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": INGEST_TRAFFIC_LINK if args.workload == "link" else None,
+                         "traffic": INGEST_TRAFFIC_LINK if (args.workload, args.counter) == ("link", "at") else None,
                          "traffic_source": "ncu capture, profiles/ingest_link.md", "kernel": "ingest",
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
                          "model": "8 B per pair + 32 B x r per distinct (aip, bip) pair",
@@ -456,7 +491,7 @@ def main():
         if breakdown:
             line["breakdown_ms"] = breakdown
         if not args.no_cpu_baseline and world == 1:
-            per_slice, text, n = oracle_slice_time(w, args.ref_sample)
+            per_slice, text, n = oracle_slice_time(w, args.ref_sample, args.counter)
             line["cpu_baseline"] = {"value": n / per_slice, "unit": "pkts/s", "cores": 1, "kind": "oracle",
                                     "sample": text}
         print(json.dumps(line), flush=True)
