@@ -31,6 +31,9 @@ METRIC = "pkts/s AT ingest+SP estimate per slice, p99 slice latency, % of sector
 N_SLICES_CYCLED = 8
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+# learned estimator: 68 used features -> 256 -> 256 -> 1 (multiply-adds x 2)
+MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch on the link
 # workload, from the ncu capture summarised in profiles/ingest_link.md (caches
 # flushed by ncu); None for other workloads or once the kernel changes
@@ -44,13 +47,15 @@ def workload_desc(w) -> dict:
             "g": w.g, "c": w.c, "u": w.u, "s": w.s, "seed": w.seed}
 
 
-def peaks():
+def peaks(kind: str = "hbm_gbs"):
+    """Measured peak (HBM GB/s, or BF16 TFLOP/s burst / sustained) and its source."""
     try:
         with open(PEAKS_PATH) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "of measured"
+        return float(p[kind]), "of measured"
     except Exception:
-        return FALLBACK_HBM_GBS, "of fallback"
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS,
+                "bf16_tflops_sustained": 1700.0}[kind], "of fallback"
 
 
 class Clocks:
@@ -243,6 +248,59 @@ def gen_batch_gpu(n: int, seed: int, n_hosts: int = 1 << 20, alpha: float = 1.1)
     return torch.where(out >= (1 << 31), out - (1 << 32), out).to(torch.int32).contiguous()
 
 
+def run_learned(args):
+    """Per-slice learned inference: the feature rows of every ATV of a
+    scanned pool (r x E rows) and the MLP on them (tcgen05 kernel).  The
+    features and the model are re-run on the same scanned state each step."""
+    import torch
+    from paper_1807_01527_gb300 import asse, build
+    build.build()
+    w = synth.workload(args.workload, seed=1)
+    stream = torch.cuda.current_stream()
+    pool = asse.Pool(w.params, stream=stream.cuda_stream)
+    pairs = w.pairs(0) if w.n_per_slice <= (8 << 20) else gen_batch_gpu(w.n_per_slice, 3, w.n_hosts, w.zipf)
+    src = torch.from_numpy(pairs.view(np.int32)).cuda() if isinstance(pairs, np.ndarray) else pairs
+    pool.ingest(src)
+    pool.scan(w.k)
+    model = asse.MLP(seed=1, stream=stream.cuda_stream)
+    rows = w.r << w.E_log2
+    x = pool.features()
+    y = torch.empty(rows, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        pool.features()
+        model.forward(x, y)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), "bench_clocks_learned.csv"), 0)
+    wall0 = time.time()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        xi = pool.features()
+        ev[i][1].record(stream)
+        model.forward(xi, y)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    model.check()
+    t_feat = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)) / 1e3
+    t_mlp = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)) / 1e3
+    peak, src_peak = peaks("bf16_tflops")
+    achieved = rows * MLP_FLOP_PER_ROW / t_mlp / 1e12
+    line = {"metric": "learned per-ATV inference: feature rows + MLP per scanned slice", "value": rows / (t_feat + t_mlp),
+            "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "mode": "learned",
+            "ms_per_step": 1e3 * (t_feat + t_mlp), "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": dict(workload_desc(w), rows_per_step=rows,
+                           l2="feature rows %d MB (fit in L2); the model's tensor-core work bounds it" % (rows * 160 >> 20)),
+            "kernel_ms": {"features": 1e3 * t_feat, "mlp_tcgen05": 1e3 * t_mlp},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "mlp_forward (tcgen05)",
+                         "peak_source": src_peak + " (bf16 burst)",
+                         "model": "2 x (68 x 256 + 256 x 256 + 256) FLOP per row"},
+            "clocks": clocks.stop(wall0, wall1)}
+    print(json.dumps(line), flush=True)
+    pool.close()
+
+
 def run_serve(args):
     """Serving: 16 independent streams (k in {4,10,30,60}, 2^14..2^18 ATVs per
     row, g in {128,512,1024}), slice batches of exponential size with mean 4 Mi
@@ -342,9 +400,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--breakdown", action="store_true", help="also time scan / restore / refresh separately")
-    ap.add_argument("--mode", default="slice", choices=["slice", "serve"],
-                    help="slice: one pool, the headline line; serve: the multi-stream serving loop")
+    ap.add_argument("--mode", default="slice", choices=["slice", "serve", "learned"],
+                    help="slice: one pool, the headline line; serve: the multi-stream serving loop; "
+                         "learned: per-slice learned inference (features + tensor-core MLP)")
     ap.add_argument("--serve-slices", type=int, default=12)
+    ap.add_argument("--cycled", type=int, default=0,
+                    help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
     ap.add_argument("--counter", default="at", choices=["at", "ace"],
                     help="at: the paper's asynchronous timestamps; ace: aging counters")
     args = ap.parse_args()
@@ -352,9 +413,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.mode == "serve":
+    if args.mode in ("serve", "learned"):
         if rank == 0:
-            run_serve(args)
+            (run_serve if args.mode == "serve" else run_learned)(args)
         return
     w = synth.workload(args.workload, seed=1 + rank)
     if args.impl == "reference":
@@ -364,7 +425,7 @@ def main():
     # inputs: distinct slices cycled through, resident in HBM (more than L2:
     # 512 MB for the link workload, about 1 GB for the long one) and the same
     # slices in pinned host memory
-    n_cycled = N_SLICES_CYCLED if w.n_per_slice <= (8 << 20) else 4
+    n_cycled = args.cycled or (N_SLICES_CYCLED if w.n_per_slice <= (8 << 20) else 4)
     host, n_distinct = make_slices(w, n_cycled)
 
     import torch

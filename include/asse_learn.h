@@ -75,8 +75,17 @@ ASSE_API int asse_mlp_set_stream(asse_mlp *mlp, void *stream);
 ASSE_API int asse_mlp_get_params(asse_mlp *mlp, float *host);
 ASSE_API int asse_mlp_set_params(asse_mlp *mlp, const float *host);
 
-/* y_dev[i] = model(x_dev[i]) for n feature rows (device buffers). */
+/* y_dev[i] = model(x_dev[i]) for n feature rows (device buffers; x_dev
+ * 16-byte aligned, row-major [n][ASSE_FEAT]).  Inference runs the whole
+ * network in one tensor-core kernel (tcgen05, accumulators in tensor memory,
+ * BF16 operands, FP32 accumulation; H1 and H2 rounded to BF16 as in
+ * training).  Stream-ordered; asse_mlp_check reports a kernel that failed.
+ * Errors: EINVAL (misaligned x_dev), ECUDA. */
 ASSE_API int asse_mlp_forward(asse_mlp *mlp, const uint16_t *x_dev, uint64_t n, float *y_dev);
+
+/* Synchronise the model's stream; ASSE_ECUDA if a kernel of this model gave
+ * up a bounded wait (its outputs are then invalid). */
+ASSE_API int asse_mlp_check(asse_mlp *mlp);
 
 /* Gradients of the mean squared error (1/n) sum (model(x_i) - t_i)^2 with
  * respect to every parameter, for n rows (device buffers); loss_dev (may be

@@ -82,6 +82,7 @@ EXPORTS = {
     "asse_mlp_backward": (i32, [vp, vp, vp, u64, vp]),
     "asse_mlp_get_grads": (i32, [vp, vp]),
     "asse_mlp_train_step": (i32, [vp, vp, vp, u64, ctypes.c_float, vp]),
+    "asse_mlp_check": (i32, [vp]),
     "asse_mlp_last_error": (ctypes.c_char_p, [vp]),
     # include/asse_serve.h
     "asse_server_create": (i32, [u64, ctypes.POINTER(vp)]),
@@ -434,11 +435,18 @@ class MLP:
         self._check(lib().asse_mlp_get_grads(self._h, vp(out.ctypes.data)))
         return out
 
-    def forward(self, x):
+    def forward(self, x, y=None):
+        """Model outputs of the feature rows x ([n][FEAT] bfloat16 on the
+        device), by the tensor-core inference kernel; stream-ordered."""
         import torch
-        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        if y is None:
+            y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         self._check(lib().asse_mlp_forward(self._h, vp(x.data_ptr()), x.shape[0], vp(y.data_ptr())))
         return y
+
+    def check(self):
+        """Synchronise; raises if a kernel of this model gave up a wait."""
+        self._check(lib().asse_mlp_check(self._h))
 
     def backward(self, x, t):
         import torch

@@ -37,8 +37,7 @@ struct Status {
     unsigned long long needed;    // tuples the overflowing join level needed
     unsigned int overflow;        // a frame exceeded the restore capacity
     unsigned int error;           // a device-side wait gave up (bounded mbarrier wait)
-    unsigned int tile_next;       // scan work queue: next tile to hand out
-    unsigned int pad[3];
+    unsigned int pad[4];
 };
 
 // A partial or complete column tuple of the restore join.

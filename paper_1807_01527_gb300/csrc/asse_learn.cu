@@ -21,6 +21,7 @@
 
 #include "../../include/asse_learn.h"
 #include "asse_device.cuh"
+#include "asse_mlp_tc.h"
 
 using bf16 = __nv_bfloat16;
 
@@ -508,6 +509,8 @@ struct asse_mlp {
     cudaStream_t stream = nullptr;
     float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
     bf16 *w1b = nullptr, *w2b = nullptr;
+    bf16 *w1p = nullptr, *w2p = nullptr;  // packed operand images of the tensor-core inference
+    int *error = nullptr;                 // set by a kernel whose wait gave up
     uint64_t cap = 0;  // rows of the activation workspace
     bf16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *y = nullptr, *dy = nullptr, *loss = nullptr;
@@ -695,6 +698,11 @@ int asse_mlp_create(uint64_t seed, void *stream, asse_mlp **out)
     alloc((void **)&m->w1b, (size_t)HID * FEAT * sizeof(bf16));
     alloc((void **)&m->w2b, (size_t)HID * HID * sizeof(bf16));
     alloc((void **)&m->loss, sizeof(float));
+    alloc((void **)&m->w1p, (size_t)HID * FEAT * sizeof(bf16));
+    alloc((void **)&m->w2p, (size_t)HID * HID * sizeof(bf16));
+    alloc((void **)&m->error, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(m->error, 0, sizeof(int), m->stream);
     if (e != cudaSuccess) {
         asse_mlp_destroy(m);
         return e == cudaErrorMemoryAllocation ? ASSE_ENOMEM : ASSE_ECUDA;
@@ -740,7 +748,7 @@ void asse_mlp_destroy(asse_mlp *m)
     cudaStreamSynchronize(m->stream);
     for (void *p : {(void *)m->params, (void *)m->grads, (void *)m->m1, (void *)m->m2, (void *)m->w1b, (void *)m->w2b,
                     (void *)m->H1, (void *)m->H2, (void *)m->dZ2, (void *)m->dZ1, (void *)m->y, (void *)m->dy,
-                    (void *)m->loss})
+                    (void *)m->loss, (void *)m->w1p, (void *)m->w2p, (void *)m->error})
         cudaFree(p);
     delete m;
 }
@@ -770,6 +778,7 @@ int asse_mlp_set_params(asse_mlp *m, const float *host)
     to_bf16_kernel<<<64, 256, 0, m->stream>>>(m->params, m->w1b, m->w2b);
     m->launches++;
     MCK(m, cudaGetLastError());
+    MCK(m, launch_mlp_pack(m->params, m->w1p, m->w2p, m->stream, &m->launches));
     MCK(m, cudaStreamSynchronize(m->stream));
     return ASSE_OK;
 }
@@ -791,13 +800,13 @@ int asse_mlp_forward(asse_mlp *m, const uint16_t *x_dev, uint64_t n, float *y_de
         return mlp_fail(m, ASSE_EINVAL, "at most 2^31-1 rows per call");
     if (n == 0)
         return ASSE_OK;
-    if (int rc = ensure_workspace(m, n < 65536 ? n : 65536))
-        return rc;
-    for (uint64_t off = 0; off < n; off += m->cap) {
-        const uint64_t c = n - off < m->cap ? n - off : m->cap;
-        if (int rc = forward(m, reinterpret_cast<const bf16 *>(x_dev) + off * FEAT, c, y_dev + off, false))
-            return rc;
-    }
+    std::string why;
+    const int rc = launch_mlp_forward_tc(reinterpret_cast<const bf16 *>(x_dev), n, m->w1p, m->w2p, m->params, y_dev,
+                                         m->error, m->stream, &m->launches, &why);
+    if (rc == 1)
+        return mlp_fail(m, ASSE_EINVAL, why);
+    if (rc != 0)
+        return mlp_fail(m, ASSE_ECUDA, why);
     return ASSE_OK;
 }
 
@@ -821,6 +830,19 @@ int asse_mlp_train_step(asse_mlp *m, const uint16_t *x_dev, const float *t_dev, 
                                            m->w2b);
     m->launches++;
     MCK(m, cudaGetLastError());
+    MCK(m, launch_mlp_pack(m->params, m->w1p, m->w2p, m->stream, &m->launches));
+    return ASSE_OK;
+}
+
+int asse_mlp_check(asse_mlp *m)
+{
+    if (!m)
+        return ASSE_EINVAL;
+    MCK(m, cudaStreamSynchronize(m->stream));
+    int flag = 0;
+    MCK(m, cudaMemcpy(&flag, m->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag)
+        return mlp_fail(m, ASSE_ECUDA, "a tensor-core MLP kernel gave up waiting for its pipeline");
     return ASSE_OK;
 }
 

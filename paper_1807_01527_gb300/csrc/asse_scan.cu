@@ -31,6 +31,7 @@
 #include <cstdint>
 
 #include "asse_device.cuh"
+#include "asse_ptx.cuh"
 
 namespace asse {
 
@@ -38,81 +39,6 @@ namespace {
 
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at 2 GHz before a wait gives up
-
-// ---------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Wait for the phase with the given parity to complete; false if it did not
-// complete within WAIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES)
-            return false;
-    return true;
-}
-
-// Global -> shared bulk copy completing on an mbarrier (16-byte aligned, size
-// a multiple of 16).
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// Shared -> global bulk copy in this thread's bulk group.
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-// Until this thread's bulk stores have read their shared-memory source.
-__device__ __forceinline__ void bulk_store_drain()
-{
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
-// Order this thread's generic-proxy shared-memory accesses before later
-// async-proxy (bulk copy) accesses of the same memory.
-__device__ __forceinline__ void fence_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // ---------------------------------------------------------------- SWAR tests
 
@@ -339,20 +265,15 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
             bulk_load(tile_buf[b] + lane * G.seg_stride, pool + (size_t)(atv0 + a) * P.Wd + q_first, G.wseg * 4u,
                       bar[b]);
     };
-    // tiles are handed out one at a time from a device-wide counter, so warps
-    // that finish early take more
-    auto grab = [&]() {
-        uint32_t t = 0;
-        if (lane == 0)
-            t = atomicAdd(&o.status->tile_next, 1u);
-        return __shfl_sync(FULL_MASK, t, 0);
-    };
-
+    // tiles are dealt round-robin over all warps of the grid: every tile
+    // costs the same, and at any moment the warps stream one contiguous
+    // stretch of the pool (a shared work counter serialises on its atomic)
+    const uint32_t n_warps = gridDim.x * G.warps;
+    uint32_t tile = blockIdx.x * G.warps + warp;
     int b = 0;
-    uint32_t tile = grab();
     if (tile < ntiles)
         issue(tile, 0);
-    uint32_t next = tile < ntiles ? grab() : ntiles;
+    uint32_t next = tile < ntiles ? tile + n_warps : ntiles;
     if (next < ntiles)
         issue(next, 1);
     while (tile < ntiles) {
@@ -458,7 +379,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
         // this buffer is free again: fetch the tile after next into it
         __syncwarp();
         tile = next;
-        next = tile < ntiles ? grab() : ntiles;
+        next = tile < ntiles ? tile + n_warps : ntiles;
         if (next < ntiles) {
             if (FUSE && P.ace)
                 bulk_store_drain();  // this buffer's write-back has read its source

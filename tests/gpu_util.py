@@ -75,3 +75,18 @@ def check_close(pool, orc, kp, *, cap_ok=True):
             # the per-frame join can stay under the cap while the total is above it
             assert res["n_candidates"] <= pool.out_cap
     return res
+
+
+def assert_state_equal(pool, orc, what="", chunk=16384):
+    """The pool's counters equal the oracle's, decoded a block of ATVs at a
+    time (a full-size pool holds up to a billion counters)."""
+    from paper_1807_01527_gb300 import asse
+    words = pool.read_pool()
+    at = orc.at()
+    info = dict(pool._info)
+    E = words.shape[1]
+    for e in range(0, E, chunk):
+        part = np.ascontiguousarray(words[:, e:e + chunk])
+        info["E"] = part.shape[1]
+        np.testing.assert_array_equal(asse.unpack_pool(part, info, pool.g), at[:, e:e + chunk],
+                                      err_msg="%s (ATVs %d..)" % (what, e))

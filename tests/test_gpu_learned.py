@@ -86,6 +86,7 @@ def test_forward_and_gradients_match_fp64_reference(mods):
     xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
     td = torch.from_numpy(t.astype(np.float32)).cuda()
     y = m.forward(xd).cpu().numpy().astype(np.float64)
+    m.check()
     y_ref, _h1, _h2 = omlp.forward(p, X)
     assert np.max(np.abs(y - y_ref)) <= 2e-3 * (1 + np.max(np.abs(y_ref)))
     loss = float(m.backward(xd, td).cpu()[0])
@@ -101,6 +102,37 @@ def test_forward_and_gradients_match_fp64_reference(mods):
         assert np.linalg.norm(a - b) <= 5e-3 * np.linalg.norm(b) + 1e-7, (name, np.linalg.norm(a - b),
                                                                           np.linalg.norm(b))
         o += k
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 19456 + 77, 262144 + 77])
+def test_tensor_core_inference_matches_fp64_reference(mods, n):
+    """The tcgen05 inference kernel on row counts around one 128-row tile,
+    one tile per SM plus a ragged tail, and many tiles per SM: every row (or
+    a sample of 4096 rows, including the last, for the largest case) against
+    the FP64 reference with BF16 rounding at the same points."""
+    asse, oracle, omlp, torch = mods
+    m = asse.MLP(seed=7)
+    rng = np.random.default_rng(n)
+    p = m.params().astype(np.float64)
+    # non-zero biases so that the bias paths are exercised
+    bias = rng.normal(scale=0.1, size=omlp.NPARAMS)
+    q = omlp.unpack(p)
+    q["b1"] += bias[:256]
+    q["b2"] += bias[256:512]
+    q["b3"] += 0.3
+    p = omlp.pack(q)
+    m.set_params(p.astype(np.float32))
+    p = m.params().astype(np.float64)
+    X = _bf16(np.abs(rng.normal(size=(n, 80))) * 0.3)
+    X[:, 68:] = 0.0
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    y = m.forward(xd)
+    m.check()
+    y = y.cpu().numpy().astype(np.float64)
+    rows = np.arange(n) if n <= 20000 else np.unique(np.concatenate([rng.integers(0, n, 4095), [n - 1]]))
+    y_ref, _h1, _h2 = omlp.forward(p, X[rows])
+    tol = 2e-3 * (1 + np.max(np.abs(y_ref)))
+    assert np.max(np.abs(y[rows] - y_ref)) <= tol, (n, np.max(np.abs(y[rows] - y_ref)))
 
 
 def test_training_beats_linear_counting(mods):
