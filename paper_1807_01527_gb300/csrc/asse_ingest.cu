@@ -1,7 +1,7 @@
 // K1: Algorithm 3 (Scan IP pair, Sec. 4.1) over a batch of (aip, bip) pairs.
 //
 // One thread takes two pairs per 128-bit streaming load (evict-first, so the
-// pair stream does not push the pool out of L2).  It first computes BH(bip)
+// pair stream does not push the pool out of L2), issued one iteration ahead.  It first computes BH(bip)
 // and looks the key (aip, BH(bip)) up in a direct-mapped table of recently
 // seen keys in shared memory: a pair whose key this block already handled in
 // this launch sets exactly the same r fields to the same values, so it is
@@ -107,19 +107,24 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     const int r = R ? R : (int)P.r;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the next iteration's pairs are loaded before this one's are processed,
+    // so the stream's DRAM latency overlaps the pool accesses
+    uint4 pr = tid < nvec ? __ldcs(pairs + tid) : make_uint4(0, 0, 0, 0);
     for (uint64_t v = tid; v < nvec; v += stride) {
-        const uint4 pr = __ldcs(pairs + v);
-        const uint32_t h0 = bip_hash(P, pr.y), h1 = bip_hash(P, pr.w);
-        const bool do0 = !seen_before(seen, pr.x, h0);
-        const bool do1 = !seen_before(seen, pr.z, h1);
+        const uint4 cur = pr;
+        if (v + stride < nvec)
+            pr = __ldcs(pairs + v + stride);
+        const uint32_t h0 = bip_hash(P, cur.y), h1 = bip_hash(P, cur.w);
+        const bool do0 = !seen_before(seen, cur.x, h0);
+        const bool do1 = !seen_before(seen, cur.z, h1);
         if (!(do0 | do1))
             continue;
         uint64_t LL0 = 0, LL1 = 0;
         uint32_t z0 = 0, z1 = 0, val0 = 0, val1 = 0;
         if (do0)
-            prep_host(P, pr.x, LL0, z0);
+            prep_host(P, cur.x, LL0, z0);
         if (do1)
-            prep_host(P, pr.z, LL1, z1);
+            prep_host(P, cur.z, LL1, z1);
         val0 = P.ace ? P.k : act_of(P, c0, act_block(P, h0));
         val1 = P.ace ? P.k : act_of(P, c0, act_block(P, h1));
         const uint32_t q0 = h0 / F, q1 = h1 / F;

@@ -157,6 +157,12 @@ __device__ RangeDesc refresh_desc(const Params &P, uint32_t q, uint32_t c0n)
     return d;
 }
 
+__device__ __forceinline__ RangeDesc load_desc(const uint4 *lo, const uint4 *hi, uint32_t x)
+{
+    const uint4 a = lo[x], b = hi[x];
+    return RangeDesc{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
 // Guard bits of the fields of word w whose value lies in one of the ranges.
 template <int WB>
 __device__ __forceinline__ void in_ranges(uint32_t w, const RangeDesc &d, uint32_t &ge_bits, uint32_t &go_bits)
@@ -225,15 +231,23 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     const uint32_t c0 = ctl->c0;
     const Refresh R = ctl->R;
     extern __shared__ __align__(128) uint8_t smem[];
-    RangeDesc *cdesc = reinterpret_cast<RangeDesc *>(smem);                 // [Wd]
-    RangeDesc *rdesc = cdesc + P.Wd;                                         // [Wd]
+    // The count ranges of word q sit in two 16-byte halves at index q + (the
+    // segment of q): the lanes of one warp read positions one segment apart,
+    // and the skew puts those reads in distinct bank groups.
+    const uint32_t n_cd = P.Wd + G.lpa;
+    uint4 *cd_lo = reinterpret_cast<uint4 *>(smem);                          // [Wd + lpa]
+    uint4 *cd_hi = cd_lo + n_cd;                                             // [Wd + lpa]
+    RangeDesc *rdesc = reinterpret_cast<RangeDesc *>(cd_hi + n_cd);          // [Wd]
     uint64_t *mbar = reinterpret_cast<uint64_t *>(rdesc + P.Wd);             // [warps][2]
     uint32_t *maskbuf = reinterpret_cast<uint32_t *>(mbar + 2 * G.warps);    // [warps][mw]
     uint32_t *tiles = reinterpret_cast<uint32_t *>(smem + G.tile_offset);    // [warps][2][tile_words]
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x) {
-        cdesc[q] = count_desc<WB>(P, q, c0, kp);
+        const RangeDesc d = count_desc<WB>(P, q, c0, kp);
+        const uint32_t x = q + q / G.wseg;
+        cd_lo[x] = make_uint4(d.lo1e, d.hih1e, d.lo1o, d.hih1o);
+        cd_hi[x] = make_uint4(d.lo2e, d.hih2e, d.lo2o, d.hih2o);
         if (FUSE)
             rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
     }
@@ -297,8 +311,11 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
             for (uint32_t i = 0; i < G.wseg; i += 4) {
                 const uint4 x = *reinterpret_cast<const uint4 *>(row + i);
                 const uint32_t q = q_first + i;
-                cnt += count_word<WB>(x.x, cdesc[q]) + count_word<WB>(x.y, cdesc[q + 1]) +
-                       count_word<WB>(x.z, cdesc[q + 2]) + count_word<WB>(x.w, cdesc[q + 3]);
+                const uint32_t xq = q + part;
+                cnt += count_word<WB>(x.x, load_desc(cd_lo, cd_hi, xq)) +
+                       count_word<WB>(x.y, load_desc(cd_lo, cd_hi, xq + 1)) +
+                       count_word<WB>(x.z, load_desc(cd_lo, cd_hi, xq + 2)) +
+                       count_word<WB>(x.w, load_desc(cd_lo, cd_hi, xq + 3));
             }
         }
         for (uint32_t off = 1; off < G.lpa; off <<= 1)
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
                 constexpr uint32_t F = 32 / WB;
                 for (uint32_t i = 0; i < G.wseg; i++) {
                     const uint32_t q = q_first + i;
-                    const uint32_t am = field_bits<WB>(row[i], cdesc[q]);
+                    const uint32_t am = field_bits<WB>(row[i], load_desc(cd_lo, cd_hi, q + part));
                     if (am) {
                         const uint32_t pos = q * F, off = pos & 31;
                         atomicOr(&my_mask[pos >> 5], am << off);
@@ -468,7 +485,7 @@ ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit)
     G.seg_stride = units * 4;
     G.apt = 32 / G.lpa;
     G.tile_words = 32 * G.seg_stride;
-    const size_t fixed = (size_t)Wd * 2 * sizeof(RangeDesc);
+    const size_t fixed = (size_t)(Wd + G.lpa) * 2 * sizeof(uint4) + (size_t)Wd * sizeof(RangeDesc);
     auto head = [&](uint32_t warps) {
         const size_t h = fixed + 2 * warps * sizeof(uint64_t) + (size_t)warps * mw * 4;
         return (h + 127) / 128 * 128;
