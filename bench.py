@@ -36,8 +36,8 @@ FALLBACK_BF16_TFLOPS = 1900.0
 MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch on the link
 # workload, from the ncu capture summarised in profiles/ingest_link.md (caches
-# flushed by ncu); None for other workloads or once the kernel changes
-INGEST_TRAFFIC_LINK = 202_667_904
+# flushed by ncu); None for other workloads or until the current kernel is captured
+INGEST_TRAFFIC_LINK = 202_521_600
 
 
 def workload_desc(w) -> dict:
@@ -286,6 +286,35 @@ def run_learned(args):
     t_mlp = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)) / 1e3
     peak, src_peak = peaks("bf16_tflops")
     achieved = rows * MLP_FLOP_PER_ROW / t_mlp / 1e12
+    # accuracy: train on synthetic states shaped like this workload's ATVs
+    # (GPU generator and training kernels), then the mean relative error on
+    # held-out states against Eq. 2's
+    keys = synth.method_keys(1)
+    n_max_log2 = 14
+    scfg = dict(k=w.k, g=w.g, r=w.r, n_max_log2=n_max_log2, bg_max=0.01, seed=11, bh_a=keys["bh_a"],
+                bh_b=keys["bh_b"])
+    xs, lns, _lcs = asse.synth_states(scfg, 0, 200_000, stream=stream.cuda_stream)
+    xt, lnt, lct = asse.synth_states(scfg, 10_000_000, 20_000, stream=stream.cuda_stream)
+    trained = asse.MLP(seed=2, stream=stream.cuda_stream)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    perm = torch.randperm(xs.shape[0], device="cuda", generator=gen)
+    bs, n_train = 4096, 600
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for step in range(n_train):
+        o = (step * bs) % xs.shape[0]
+        idx = perm[o:o + bs]
+        trained.train_step(xs[idx].contiguous(), lns[idx].contiguous(), 2e-3 if step < 400 else 5e-4)
+    t1.record(stream)
+    yt = trained.forward(xt)
+    trained.check()
+    n_true = torch.exp(lnt)
+    acc = {"states": "k=%d, g=%d, cardinalities log-uniform in [1, 2^%d], background <= 1%% per AT and slice"
+                     % (w.k, w.g, n_max_log2),
+           "train_rows": n_train * bs, "train_ms": t0.elapsed_time(t1),
+           "mre_mlp": torch.mean(torch.abs(torch.exp(yt) - n_true) / n_true).item(),
+           "mre_eq2": torch.mean(torch.abs(lct - n_true) / n_true).item(), "held_out": int(xt.shape[0])}
     line = {"metric": "learned per-ATV inference: feature rows + MLP per scanned slice", "value": rows / (t_feat + t_mlp),
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "mode": "learned",
             "ms_per_step": 1e3 * (t_feat + t_mlp), "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
@@ -296,6 +325,7 @@ def run_learned(args):
                          "frac": achieved / peak, "traffic": None, "kernel": "mlp_forward (tcgen05)",
                          "peak_source": src_peak + " (bf16 burst)",
                          "model": "2 x (68 x 256 + 256 x 256 + 256) FLOP per row"},
+            "accuracy": acc,
             "clocks": clocks.stop(wall0, wall1)}
     print(json.dumps(line), flush=True)
     pool.close()
@@ -471,16 +501,23 @@ def main():
     start.record(stream)
     pairs_done = 0
     n_reported = 0
+    host_t = {"ingest_call": [], "close_call": [], "report_call": []}
     for i in range(args.steps):
         src = dev[(args.warmup + i) % n_cycled]
         ev[i][0].record(stream)
+        h0 = time.perf_counter()
         pool.ingest(src)
         ev[i][1].record(stream)
         t0 = time.perf_counter()
         pool.close_slice(w.k)
         ev[i][2].record(stream)
+        t1 = time.perf_counter()
         rep = pool.report()
-        lat.append(time.perf_counter() - t0)
+        t2 = time.perf_counter()
+        lat.append(t2 - t0)
+        host_t["ingest_call"].append(t0 - h0)
+        host_t["close_call"].append(t1 - t0)
+        host_t["report_call"].append(t2 - t1)
         n_reported += rep.size
         pairs_done += n_pairs[(args.warmup + i) % n_cycled]
     end.record(stream)
@@ -535,7 +572,11 @@ def main():
             "slice_latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                                      int(0.99 * len(lat_ms)))],
                                  "what": "close_slice call to report on the host"},
-            "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * cls},
+            "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * cls,
+                          "ingest_p50": 1e3 * statistics.median(t_ingest), "close_p50": 1e3 * statistics.median(t_close),
+                          "what": "CUDA events on the pool's stream around each call; an ingest recorded right "
+                                  "after the host waited for a report also holds its launch latency"},
+            "host_call_ms_p50": {k: 1e3 * statistics.median(v) for k, v in host_t.items()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": INGEST_TRAFFIC_LINK if (args.workload, args.counter) == ("link", "at") else None,

@@ -58,6 +58,19 @@ typedef struct asse_synth_cfg {
  * kp <= 64.  Errors: ESTATE, EINVAL, ECUDA. */
 ASSE_API int asse_features(asse_pool *pool, uint16_t *x_dev);
 
+/* Learned cardinality estimate of every ATV of a pool, for the window of
+ * the last asse_scan: the feature rows (written to x_dev, [r*E][ASSE_FEAT]
+ * bf16, 16-byte aligned), the model on them, and est_dev[i] = exp(model) where
+ * the model is inside its training range (the ATV not saturated and
+ * 0 <= model <= max_log_n, the log of the largest cardinality it was trained
+ * on), else Eq. 2's linear-counting estimate from the ATV's count (a
+ * saturated count g taken as g - 1/2).  *n_fallback_dev (device) receives
+ * the number of ATVs that fell back to Eq. 2.  The model must run on the
+ * pool's stream.  Same validity window as asse_features.
+ * Errors: ESTATE, EINVAL, ECUDA. */
+ASSE_API int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, uint16_t *x_dev,
+                                   float *est_dev, uint32_t *n_fallback_dev);
+
 /* States first .. first+n-1 of a synthetic set: features x_dev [n][FEAT]
  * bf16, labels log_n_dev [n] = ln(n) and the Eq. 2 estimate of each state's
  * count lc_dev [n] (a saturated count g is taken as g - 1/2).  All device

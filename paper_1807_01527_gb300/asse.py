@@ -72,6 +72,7 @@ EXPORTS = {
     "asse_strerror": (ctypes.c_char_p, [i32]),
     # include/asse_learn.h
     "asse_features": (i32, [vp, vp]),
+    "asse_estimate_learned": (i32, [vp, vp, ctypes.c_float, vp, vp, vp]),
     "asse_synth_states": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
     "asse_mlp_create": (i32, [u64, vp, ctypes.POINTER(vp)]),
     "asse_mlp_destroy": (None, [vp]),
@@ -315,7 +316,7 @@ class Pool:
             rc = fn(self._h, vp(out.data_ptr()), out.numel() * out.element_size() // 16, ctypes.byref(n), DEVICE)
             self._check(rc, int(n.value))
             return int(n.value)
-        buf = np.zeros(self.out_cap, dtype=SP_DTYPE)
+        buf = np.empty(self.out_cap, dtype=SP_DTYPE)
         rc = fn(self._h, vp(buf.ctypes.data), self.out_cap, ctypes.byref(n), HOST)
         self._check(rc, int(n.value))
         return buf[: int(n.value)]
@@ -370,6 +371,19 @@ class Pool:
 
     def load(self, image: bytes):
         self._check(lib().asse_load(self._h, image, len(image)))
+
+    def estimate_learned(self, model, max_log_n: float):
+        """Per-ATV learned cardinality estimates [r*E] (torch float32 on the
+        device) with the Eq. 2 fallback outside the model's training range,
+        and the number of ATVs that fell back; between scan() and advance()."""
+        import torch
+        rows = self.r * self._info["E"]
+        x = torch.empty((rows, FEAT), dtype=torch.bfloat16, device="cuda")
+        est = torch.empty(rows, dtype=torch.float32, device="cuda")
+        nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self._check(lib().asse_estimate_learned(self._h, model._h, float(max_log_n), vp(x.data_ptr()),
+                                                vp(est.data_ptr()), vp(nfb.data_ptr())))
+        return est, nfb, x
 
     def features(self):
         """Feature rows [r*E][FEAT] (torch bfloat16 on the device) of every

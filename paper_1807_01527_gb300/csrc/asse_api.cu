@@ -323,6 +323,7 @@ int pool_feature_view(asse_pool *p, FeatureView *v)
     v->c0 = (uint32_t)(p->t % (2 * p->cfg.k));
     v->kp = p->scan_kp;
     v->aat = p->aat;
+    v->cnt = p->cnt;
     v->stream = p->stream;
     v->launches = &p->launches;
     v->sms = p->sms;

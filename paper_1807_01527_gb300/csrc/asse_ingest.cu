@@ -63,12 +63,15 @@ __device__ __forceinline__ void prep_host(const Params &P, uint32_t aip, uint64_
 __device__ __forceinline__ uint32_t *field_word(const Params &P, uint32_t *pool, int i, uint32_t z, uint64_t LL,
                                                 uint32_t q)
 {
-    return pool + (((uint64_t)i << P.E_log2) + ((z << P.c) | column(P, LL, i))) * P.Wd + q;
+    const uint32_t atv = ((uint32_t)i << P.E_log2) | (z << P.c) | column(P, LL, i);
+    return pool + (uint64_t)atv * P.Wd + q;
 }
 
 constexpr int INGEST_THREADS = 1024;
+constexpr int INGEST_WARPS = INGEST_THREADS / 32;
 constexpr int INGEST_BLOCKS_PER_SM = 1;
 constexpr uint32_t SEEN_LOG2 = 14;  // 16,384 keys = 128 KB of shared memory per block
+constexpr uint32_t QCAP = 128;      // per-warp queue of new keys (below 64 between rounds, + 64)
 constexpr unsigned long long NO_KEY = ~0ull;  // BH values are < 2^16, so never a real key
 
 __device__ __forceinline__ uint32_t seen_slot(uint32_t aip, uint32_t h)
@@ -87,6 +90,53 @@ __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t a
     return false;
 }
 
+// Algorithm 3 for two keys (aip, h = BH(bip)) of this lane, each if its ok
+// flag is set: f(aip), the r column windows, the ACT of AT h, then the r word
+// loads of both keys together and the field sets.
+template <int WB, int R>
+__device__ __forceinline__ void set_keys(const Params &P, uint32_t *pool, uint32_t c0, int r, uint32_t aip0,
+                                         uint32_t h0, bool ok0, uint32_t aip1, uint32_t h1, bool ok1)
+{
+    constexpr uint32_t F = 32 / WB;
+    constexpr uint32_t FM = (1u << WB) - 1;
+    constexpr int RM = R ? R : 8;
+    uint64_t LL0 = 0, LL1 = 0;
+    uint32_t z0 = 0, z1 = 0;
+    if (ok0)
+        prep_host(P, aip0, LL0, z0);
+    if (ok1)
+        prep_host(P, aip1, LL1, z1);
+    const uint32_t val0 = P.ace ? P.k : act_of(P, c0, act_block(P, h0));
+    const uint32_t val1 = P.ace ? P.k : act_of(P, c0, act_block(P, h1));
+    const uint32_t q0 = h0 / F, q1 = h1 / F;
+    const uint32_t sh0 = (h0 - q0 * F) * WB, sh1 = (h1 - q1 * F) * WB;
+    uint32_t *a0[RM], *a1[RM];
+    uint32_t o0[RM], o1[RM];
+#pragma unroll
+    for (int i = 0; i < RM; i++) {
+        if (i < r) {
+            a0[i] = field_word(P, pool, i, z0, LL0, q0);
+            a1[i] = field_word(P, pool, i, z1, LL1, q1);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; i++) {
+        if (i < r) {
+            o0[i] = ok0 ? *a0[i] : 0u;
+            o1[i] = ok1 ? *a1[i] : 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; i++) {
+        if (i < r) {
+            if (ok0)
+                set_field(a0[i], o0[i], sh0, val0, FM);
+            if (ok1)
+                set_field(a1[i], o1[i], sh1, val1, FM);
+        }
+    }
+}
+
 template <int WB, int R>
 __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     ingest_kernel(Params P, uint32_t *pool, const uint32_t *__restrict__ pairs_raw, uint64_t n_arg,
@@ -97,69 +147,65 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     const uint64_t nvec = n / 2;
     const uint4 *__restrict__ pairs = reinterpret_cast<const uint4 *>(pairs_raw);
     const uint2 *__restrict__ tail = (n & 1) ? reinterpret_cast<const uint2 *>(pairs_raw + 2 * (n - 1)) : nullptr;
-    constexpr uint32_t F = 32 / WB;
     constexpr uint32_t FM = (1u << WB) - 1;
-    constexpr int RM = R ? R : 8;
     extern __shared__ unsigned long long seen[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint2 *queue = reinterpret_cast<uint2 *>(seen + (1u << SEEN_LOG2)) + warp * QCAP;
     for (uint32_t i = threadIdx.x; i < (1u << SEEN_LOG2); i += blockDim.x)
         seen[i] = NO_KEY;
     __syncthreads();
     const int r = R ? R : (int)P.r;
+    // Warp-uniform loop: the 32 lanes of a warp take 32 consecutive vectors.
+    // Keys the table has not seen go to the warp's queue; whenever it holds
+    // 64 of them, every lane runs Algorithm 3 on two, so the long path runs
+    // with all lanes busy however many repeats the table removed.
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // the next iteration's pairs are loaded before this one's are processed,
+    const uint64_t base0 = (uint64_t)blockIdx.x * blockDim.x + warp * 32u;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t qn = 0;
+    // the next round's pairs are loaded before this round's are processed,
     // so the stream's DRAM latency overlaps the pool accesses
-    uint4 pr = tid < nvec ? __ldcs(pairs + tid) : make_uint4(0, 0, 0, 0);
-    for (uint64_t v = tid; v < nvec; v += stride) {
+    uint4 pr = base0 + lane < nvec ? __ldcs(pairs + base0 + lane) : make_uint4(0, 0, 0, 0);
+    for (uint64_t vb = base0; vb < nvec; vb += stride) {
+        const uint64_t v = vb + lane;
         const uint4 cur = pr;
         if (v + stride < nvec)
             pr = __ldcs(pairs + v + stride);
-        const uint32_t h0 = bip_hash(P, cur.y), h1 = bip_hash(P, cur.w);
-        const bool do0 = !seen_before(seen, cur.x, h0);
-        const bool do1 = !seen_before(seen, cur.z, h1);
-        if (!(do0 | do1))
-            continue;
-        uint64_t LL0 = 0, LL1 = 0;
-        uint32_t z0 = 0, z1 = 0, val0 = 0, val1 = 0;
+        bool do0 = false, do1 = false;
+        uint32_t h0 = 0, h1 = 0;
+        if (v < nvec) {
+            h0 = bip_hash(P, cur.y);
+            h1 = bip_hash(P, cur.w);
+            do0 = !seen_before(seen, cur.x, h0);
+            do1 = !seen_before(seen, cur.z, h1);
+        }
+        const unsigned m0 = __ballot_sync(FULL_MASK, do0), m1 = __ballot_sync(FULL_MASK, do1);
         if (do0)
-            prep_host(P, cur.x, LL0, z0);
+            queue[qn + __popc(m0 & lt)] = make_uint2(cur.x, h0);
+        qn += __popc(m0);
         if (do1)
-            prep_host(P, cur.z, LL1, z1);
-        val0 = P.ace ? P.k : act_of(P, c0, act_block(P, h0));
-        val1 = P.ace ? P.k : act_of(P, c0, act_block(P, h1));
-        const uint32_t q0 = h0 / F, q1 = h1 / F;
-        const uint32_t sh0 = (h0 - q0 * F) * WB, sh1 = (h1 - q1 * F) * WB;
-        uint32_t *a0[RM], *a1[RM];
-        uint32_t o0[RM], o1[RM];
-#pragma unroll
-        for (int i = 0; i < RM; i++) {
-            if (i < r) {
-                a0[i] = field_word(P, pool, i, z0, LL0, q0);
-                a1[i] = field_word(P, pool, i, z1, LL1, q1);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < RM; i++) {
-            if (i < r) {
-                o0[i] = do0 ? *a0[i] : 0u;
-                o1[i] = do1 ? *a1[i] : 0u;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < RM; i++) {
-            if (i < r) {
-                if (do0)
-                    set_field(a0[i], o0[i], sh0, val0, FM);
-                if (do1)
-                    set_field(a1[i], o1[i], sh1, val1, FM);
-            }
+            queue[qn + __popc(m1 & lt)] = make_uint2(cur.z, h1);
+        qn += __popc(m1);
+        if (qn >= 64) {
+            __syncwarp();
+            qn -= 64;
+            const uint2 e0 = queue[qn + lane], e1 = queue[qn + 32 + lane];
+            __syncwarp();
+            set_keys<WB, R>(P, pool, c0, r, e0.x, e0.y, true, e1.x, e1.y, true);
         }
     }
-    if (tail != nullptr && tid == 0) {
-        const uint2 pr = *tail;
+    __syncwarp();
+    if (qn > 0) {
+        const bool ok0 = lane < qn, ok1 = lane + 32 < qn;
+        const uint2 e0 = ok0 ? queue[lane] : make_uint2(0, 0);
+        const uint2 e1 = ok1 ? queue[lane + 32] : make_uint2(0, 0);
+        set_keys<WB, R>(P, pool, c0, r, e0.x, e0.y, ok0, e1.x, e1.y, ok1);
+    }
+    if (tail != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint2 pr1 = *tail;
         uint64_t LL;
         uint32_t z, q, sh, val;
-        prep_pair<WB>(P, c0, pr.x, pr.y, LL, z, q, sh, val);
+        prep_pair<WB>(P, c0, pr1.x, pr1.y, LL, z, q, sh, val);
         for (int i = 0; i < r; i++) {
             uint32_t *a = field_word(P, pool, i, z, LL, q);
             set_field(a, *a, sh, val, FM);
@@ -177,7 +223,7 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
         return cudaSuccess;
     const uint64_t nvec = n / 2;
     *launches += 1;
-    const size_t smem = sizeof(unsigned long long) << SEEN_LOG2;
+    const size_t smem = (sizeof(unsigned long long) << SEEN_LOG2) + (size_t)INGEST_WARPS * QCAP * sizeof(uint2);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         auto kern = P.r == 4 ? ingest_kernel<WB, 4> : ingest_kernel<WB, 0>;

@@ -171,6 +171,7 @@ struct FeatureView {
     const uint32_t *pool;
     uint32_t c0, kp;
     const unsigned long long *aat;
+    const uint16_t *cnt;  // |ATV|^{k'} of every ATV, from the same scan
     cudaStream_t stream;
     uint64_t *launches;
     int sms;

@@ -45,22 +45,25 @@ static_assert(NPARAMS == ASSE_MLP_NPARAMS, "parameter layout");
 
 // Feature row of one ATV from its packed words (global or shared), computed
 // by one warp: active ATs per age (Algorithm 1 for the latest kp slices) and
-// their total, then the three load features.
+// their total, then the three load features.  Each lane counts ages in its
+// own column of hist ([64][32] 16-bit counters, zero on entry and left zero), so the
+// histogram needs no atomics; the lanes then add up one age row each,
+// reading the row rotated by the age so that no two lanes hit one bank.
+constexpr uint32_t HIST_WORDS = 64 * 32 / 2;  // [64][32] 16-bit counters (a lane counts at most g/32 <= 128)
+
 template <int WB>
-__device__ void atv_features(const Params &P, const uint32_t *words, uint32_t c0, uint32_t kp, float lp, float lup,
-                             float lmean, uint32_t *hist, bf16 *row, uint32_t lane, uint32_t *cnt_out)
+__device__ void atv_features(const Params &P, const uint32_t *words, const uint8_t *act_tab, uint32_t kp, float lp,
+                             float lup, float lmean, uint16_t *hist, bf16 *row, uint32_t lane, uint32_t *cnt_out)
 {
     constexpr uint32_t F = 32 / WB;
     constexpr uint32_t FM = (1u << WB) - 1;
-    for (uint32_t i = lane; i < 64; i += 32)
-        hist[i] = 0;
-    __syncwarp();
     uint32_t cnt = 0;
     const uint32_t nw = (P.g + F - 1) / F;
     for (uint32_t q = lane; q < nw; q += 32) {
         const uint32_t w = words[q];
-        for (uint32_t j = 0; j < F; j++) {
-            const uint32_t h = q * F + j;
+        uint32_t h = q * F;
+#pragma unroll
+        for (uint32_t j = 0; j < F; j++, h++) {
             if (h >= P.g)
                 break;
             const uint32_t v = (w >> (j * WB)) & FM;
@@ -70,27 +73,49 @@ __device__ void atv_features(const Params &P, const uint32_t *words, uint32_t c0
                 active = v + kp >= P.k + 1;  // a counter visited age slices ago holds k - age
                 age = P.k - v;
             } else {
-                uint32_t d = act_of(P, c0, act_block(P, h)) + P.k2 - v;
+                uint32_t d = act_tab[h] + P.k2 - v;  // (ACT of the AT's block - v) mod 2k
                 d = d >= P.k2 ? d - P.k2 : d;
                 active = v < P.k2 && d < kp;
                 age = d;
             }
             if (active) {
                 cnt++;
-                if (age < 64)
-                    atomicAdd(&hist[age], 1u);
+                hist[age * 32 + lane] += 1;
             }
         }
     }
     cnt = __reduce_add_sync(FULL_MASK, cnt);
     __syncwarp();
+    uint32_t bins[2] = {0, 0};
+#pragma unroll
+    for (uint32_t t = 0; t < 2; t++) {
+        const uint32_t e = lane + 32 * t;
+        if (e < kp) {
+            uint16_t *hr = hist + e * 32;
+            uint32_t acc = 0;
+            for (uint32_t j = 0; j < 32; j++) {
+                const uint32_t c = (j + e) & 31;
+                acc += hr[c];
+                hr[c] = 0;
+            }
+            bins[t] = acc;
+        }
+    }
     const float inv_g = 1.0f / (float)P.g;
-    for (uint32_t e = lane; e < FEAT; e += 32) {
+#pragma unroll
+    for (uint32_t m = 0; m < (FEAT + 31) / 32; m++) {
+        const uint32_t e = lane + 32 * m;
+        // age e - 1 is held by lane (e - 1) mod 32, in bins[(e - 1) / 32]
+        const uint32_t src = (e + 31) & 31;
+        const uint32_t b0 = __shfl_sync(FULL_MASK, bins[0], src);
+        const uint32_t b1 = __shfl_sync(FULL_MASK, bins[1], src);
+        if (e >= FEAT)
+            continue;
         float v = 0.0f;
         if (e == 0)
             v = (float)cnt * inv_g;
         else if (e <= 64)
-            v = (float)hist[e - 1] * inv_g;
+            v = (float)(e - 1 < 32 ? b0 : b1) * inv_g;
         else if (e == 65)
             v = lp;
         else if (e == 66)
@@ -104,26 +129,65 @@ __device__ void atv_features(const Params &P, const uint32_t *words, uint32_t c0
     __syncwarp();
 }
 
+constexpr int FEAT_WARPS = 8;
+
 template <int WB>
-__global__ void __launch_bounds__(256) features_kernel(Params P, const uint32_t *pool, uint32_t c0, uint32_t kp,
-                                                       const unsigned long long *aat, bf16 *x, uint32_t total_atv)
+__global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, const uint32_t *pool, uint32_t c0,
+                                                                   uint32_t kp, const unsigned long long *aat, bf16 *x,
+                                                                   uint32_t total_atv)
 {
-    __shared__ uint32_t hist[8][64];
+    extern __shared__ uint32_t fsm[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint16_t *hist = reinterpret_cast<uint16_t *>(fsm + warp * HIST_WORDS);
+    // load features of every (row, frame), then UP and mean P of every frame,
+    // once per block (FP64, then stored as FP32)
+    float *ltab = reinterpret_cast<float *>(fsm + FEAT_WARPS * HIST_WORDS);
+    uint8_t *act_tab = reinterpret_cast<uint8_t *>(ltab + (P.r + 2) * P.nf);  // [g]: ACT of each AT's block
+    for (uint32_t h = threadIdx.x; h < P.g; h += blockDim.x)
+        act_tab[h] = (uint8_t)act_of(P, c0, act_block(P, h));
     const double denom = (double)P.g * (double)(P.cmask + 1);
-    for (uint32_t atv = blockIdx.x * 8 + warp; atv < total_atv; atv += gridDim.x * 8) {
-        const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
-        double up = 1.0, sum = 0.0, mine = 0.0;
+    for (uint32_t frame = threadIdx.x; frame < P.nf; frame += blockDim.x) {
+        double up = 1.0, sum = 0.0;
         for (uint32_t i = 0; i < P.r; i++) {
             const double pi = (double)aat[(size_t)i * P.nf + frame] / denom;
             up *= pi;
             sum += pi;
-            if (i == row)
-                mine = pi;
+            ltab[i * P.nf + frame] = (float)pi;
         }
-        atv_features<WB>(P, pool + (size_t)atv * P.Wd, c0, kp, (float)mine, (float)up, (float)(sum / P.r),
-                         hist[warp], x + (size_t)atv * FEAT, lane, nullptr);
+        ltab[P.r * P.nf + frame] = (float)up;
+        ltab[(P.r + 1) * P.nf + frame] = (float)(sum / P.r);
     }
+    for (uint32_t i = lane; i < HIST_WORDS; i += 32)
+        fsm[warp * HIST_WORDS + i] = 0;
+    __syncthreads();
+    for (uint32_t atv = blockIdx.x * FEAT_WARPS + warp; atv < total_atv; atv += gridDim.x * FEAT_WARPS) {
+        const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
+        atv_features<WB>(P, pool + (size_t)atv * P.Wd, act_tab, kp, ltab[row * P.nf + frame], ltab[P.r * P.nf + frame],
+                         ltab[(P.r + 1) * P.nf + frame], hist, x + (size_t)atv * FEAT, lane, nullptr);
+    }
+}
+
+// est[i] = exp(y[i]) where the model is inside its training range (the ATV
+// not saturated and 0 <= y <= max_log_n), else the linear-counting estimate
+// of Eq. 2 from the ATV's count (a saturated count g taken as g - 1/2).
+__global__ void learned_combine_kernel(const float *y, const uint16_t *cnt, uint32_t g, float max_log_n,
+                                       uint64_t n, float *est, uint32_t *n_fallback)
+{
+    uint32_t fb = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float yi = y[i];
+        const uint32_t c = cnt[i];
+        if (c < g && yi >= 0.0f && yi <= max_log_n) {
+            est[i] = expf(yi);
+        } else {
+            const double cc = c >= g ? (double)g - 0.5 : (double)c;
+            est[i] = (float)(-(double)g * log(((double)g - cc) / (double)g));
+            fb++;
+        }
+    }
+    fb = __reduce_add_sync(FULL_MASK, fb);
+    if ((threadIdx.x & 31) == 0 && fb)
+        atomicAdd(n_fallback, fb);
 }
 
 // ---------------------------------------------------------------- synthetic states
@@ -169,11 +233,19 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
     extern __shared__ uint32_t sm[];
     int16_t *last = reinterpret_cast<int16_t *>(sm);                // [g]
     uint32_t *words = sm + (P.g + 1) / 2;                           // [Wd]
-    uint32_t *hist = words + P.Wd;                                   // [64]
+    uint32_t *hist_w = words + P.Wd;                                 // [64][32] 16-bit, kept zero between uses
+    uint16_t *hist = reinterpret_cast<uint16_t *>(hist_w);
+    uint8_t *act_tab = reinterpret_cast<uint8_t *>(hist_w + HIST_WORDS);  // [g]: ACT of each AT's block
     __shared__ uint32_t end[65];
     __shared__ uint32_t card;
     __shared__ float pbg;
     const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < HIST_WORDS; i += blockDim.x)
+        hist_w[i] = 0;
+    // the states are packed as of the end of slice k - 1 (block 0's ACT (k-1) mod 2k)
+    for (uint32_t h = tid; h < P.g; h += blockDim.x)
+        act_tab[h] = (uint8_t)act_of(P, (P.k - 1) % P.k2, act_block(P, h));
+    __syncthreads();
     for (uint64_t si = blockIdx.x; si < n; si += gridDim.x) {
         const uint64_t key = splitmix(S.seed ^ splitmix(first + si + 0x51ED270B27ull));
         if (tid == 0) {
@@ -222,7 +294,7 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
         if (tid < 32) {
             const float pw = 1.0f - powf(1.0f - pbg, (float)P.k);  // background activity over the window
             uint32_t cnt = 0;
-            atv_features<WB>(P, words, (P.k - 1) % P.k2, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
+            atv_features<WB>(P, words, act_tab, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
                              tid, &cnt);
             if (tid == 0) {
                 log_n[si] = (float)log((double)card);
@@ -629,14 +701,50 @@ int asse_features(asse_pool *pool, uint16_t *x_dev)
     const uint32_t total = v.P.r << v.P.E_log2;
     cudaError_t e = dispatch_w(v.w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        const unsigned grid = (unsigned)v.sms * 8;
-        features_kernel<WB><<<grid, 256, 0, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
-                                                         reinterpret_cast<bf16 *>(x_dev), total);
+        const size_t smem = ((size_t)FEAT_WARPS * HIST_WORDS + (size_t)(v.P.r + 2) * v.P.nf) * sizeof(uint32_t) +
+                            v.P.g;
+        cudaError_t e2 = cudaFuncSetAttribute(features_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem);
+        if (e2 != cudaSuccess)
+            return e2;
+        const unsigned grid = (unsigned)v.sms * 4;
+        features_kernel<WB><<<grid, FEAT_WARPS * 32, smem, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
+                                                                       reinterpret_cast<bf16 *>(x_dev), total);
         return cudaGetLastError();
     });
     *v.launches += 1;
     if (e != cudaSuccess)
         return pool_fail(pool, ASSE_ECUDA, std::string("features launch: ") + cudaGetErrorString(e));
+    return ASSE_OK;
+}
+
+int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, uint16_t *x_dev, float *est_dev,
+                          uint32_t *n_fallback_dev)
+{
+    if (!pool || !mlp || !x_dev || !est_dev || !n_fallback_dev || !(max_log_n >= 0.0f))
+        return pool ? pool_fail(pool, ASSE_EINVAL, "NULL argument or negative max_log_n") : ASSE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(x_dev) & 15u) != 0)
+        return pool_fail(pool, ASSE_EINVAL, "x_dev must be 16-byte aligned");
+    FeatureView v;
+    if (int rc = pool_feature_view(pool, &v))
+        return rc;
+    if (mlp->stream != v.stream)
+        return pool_fail(pool, ASSE_EINVAL, "the model and the pool must use the same stream");
+    if (int rc = asse_features(pool, x_dev))
+        return rc;
+    const uint64_t total = (uint64_t)v.P.r << v.P.E_log2;
+    // the model's outputs go to est_dev first, then are replaced in place
+    if (int rc = asse_mlp_forward(mlp, x_dev, total, est_dev))
+        return pool_fail(pool, rc, std::string("model: ") + mlp->err);
+    if (cudaMemsetAsync(n_fallback_dev, 0, sizeof(uint32_t), v.stream) != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, "memset of the fallback counter failed");
+    const unsigned grid = (unsigned)v.sms * 4;
+    learned_combine_kernel<<<grid, 256, 0, v.stream>>>(est_dev, v.cnt, v.P.g, max_log_n, total, est_dev,
+                                                       n_fallback_dev);
+    *v.launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, std::string("learned combine launch: ") + cudaGetErrorString(e));
     return ASSE_OK;
 }
 
@@ -663,7 +771,7 @@ int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uin
     const uint32_t Fw = 32 / w;
     P.Wd = ((cfg->g + Fw - 1) / Fw + 7) / 8 * 8;
     SynthArgs S{cfg->seed, cfg->n_max_log2, cfg->bg_max};
-    const size_t smem = ((cfg->g + 1) / 2 + P.Wd + 64) * sizeof(uint32_t);
+    const size_t smem = ((cfg->g + 1) / 2 + P.Wd + HIST_WORDS) * sizeof(uint32_t) + cfg->g;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

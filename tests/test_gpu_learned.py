@@ -154,3 +154,44 @@ def test_training_beats_linear_counting(mods):
     mre_mlp = torch.mean(torch.abs(torch.exp(y) - n_true) / n_true).item()
     mre_lc = torch.mean(torch.abs(lct - n_true) / n_true).item()
     assert mre_mlp < mre_lc, (mre_mlp, mre_lc)
+
+
+def test_learned_estimate_with_fallback(mods):
+    """asse_estimate_learned: the model's output where it is inside its
+    training range, Eq. 2 from the ATV's count elsewhere (saturated ATVs and
+    outputs above max_log_n), on a pool with saturated and light ATVs."""
+    asse, oracle, omlp, torch = mods
+    g = 128
+    p = dict(k=4, theta=40, g=g, r=4, c=8, u=0, s=8, **synth.method_keys(4))
+    stream = torch.cuda.current_stream().cuda_stream
+    pool = asse.Pool(p, stream=stream)
+    m = asse.MLP(seed=3, stream=stream)
+    orc = oracle.Oracle.from_params(p)
+    for t in range(5):
+        pairs = mixed_pairs(11, t, 20001, [20, 60, 400, 5000])
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        pool.scan(4)
+        # shift the output bias so the model's outputs straddle the training
+        # range: some inside, some above, some below
+        y0 = m.forward(pool.features()).cpu().numpy().astype(np.float64)
+        prm = m.params()
+        prm[-1] += np.float32(1.0 - np.median(y0))
+        m.set_params(prm)
+        y1 = y0 + (1.0 - np.median(y0))
+        max_log_n = float(np.quantile(y1, 0.75))
+        est, nfb, x = pool.estimate_learned(m, max_log_n)
+        y = m.forward(x).cpu().numpy().astype(np.float64)
+        cnt = orc.counts(4).reshape(-1).astype(np.float64)
+        inside = (cnt < g) & (y >= 0.0) & (y <= max_log_n)
+        c = np.where(cnt >= g, g - 0.5, cnt)
+        lc = -g * np.log((g - c) / g)
+        want = np.where(inside, np.exp(y), lc)
+        got = est.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-5)
+        assert int(nfb.item()) == int((~inside).sum())
+        if t >= 2:
+            assert (cnt >= g).any() and inside.any()
+        pool.restore()
+        pool.advance()
+        orc.advance()
