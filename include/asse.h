@@ -153,6 +153,25 @@ ASSE_API int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int
  * Errors: EINVAL (kp), ECUDA. */
 ASSE_API int asse_close_slice(asse_pool *pool, uint32_t kp);
 
+#define ASSE_MAX_WINDOWS 4
+
+/* asse_close_slice for several windows at once: the same ATs answer every
+ * window k' <= k (Sec. 3, Algorithm 1), so one pass over the pool counts
+ * |ATV|^{k'} for each kps[i] (1 <= kps[i] <= k, 1 <= n_windows <=
+ * ASSE_MAX_WINDOWS), with the refresh fused as in asse_close_slice; then the
+ * restore, NAT and Eq. 4 of each window; then slice t+1 opens.  The first
+ * call with a given number of windows allocates the extra windows' outputs
+ * (the size of asse_close_slice's outputs each).  Results of window i are read
+ * with asse_report, asse_candidates, asse_counts and asse_loads after
+ * asse_select_window(pool, i); window 0 is selected on return.  Asynchronous.
+ * Errors: EINVAL (kps, n_windows), ENOMEM, ECUDA. */
+ASSE_API int asse_close_slice_multi(asse_pool *pool, const uint32_t *kps, uint32_t n_windows);
+
+/* Make the readers (asse_report, asse_candidates, asse_counts, asse_loads)
+ * return window `window` of the last close.  Errors: EINVAL (window >= the
+ * number of windows of the last close; a plain close or scan has one). */
+ASSE_API int asse_select_window(asse_pool *pool, uint32_t window);
+
 /* Stepwise close, part 1: the scan of asse_close_slice without the refresh.
  * The pool state is unchanged.  Asynchronous.  Errors: EINVAL, ECUDA. */
 ASSE_API int asse_scan(asse_pool *pool, uint32_t kp);

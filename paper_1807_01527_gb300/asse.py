@@ -54,6 +54,8 @@ EXPORTS = {
     "asse_set_stream": (i32, [vp, vp]),
     "asse_ingest": (i32, [vp, vp, u64, i32]),
     "asse_close_slice": (i32, [vp, u32]),
+    "asse_close_slice_multi": (i32, [vp, vp, u32]),
+    "asse_select_window": (i32, [vp, u32]),
     "asse_scan": (i32, [vp, u32]),
     "asse_restore": (i32, [vp]),
     "asse_advance": (i32, [vp]),
@@ -299,6 +301,16 @@ class Pool:
 
     def close_slice(self, kp: int | None = None):
         self._check(lib().asse_close_slice(self._h, self.k if kp is None else kp))
+
+    def close_slice_multi(self, kps):
+        """Close the open slice for several windows k' in one scan pass;
+        window 0 is selected for the readers afterwards."""
+        arr = (ctypes.c_uint32 * len(kps))(*[int(k) for k in kps])
+        self._check(lib().asse_close_slice_multi(self._h, arr, len(kps)))
+
+    def select_window(self, i: int):
+        """Make report / candidates / counts / loads return window i of the last close."""
+        self._check(lib().asse_select_window(self._h, int(i)))
 
     def scan(self, kp: int | None = None):
         self._check(lib().asse_scan(self._h, self.k if kp is None else kp))

@@ -54,6 +54,16 @@ struct asse_pool {
     uint32_t *q_aips = nullptr;
     asse_superpoint *q_out = nullptr;
     uint64_t q_cap = 0;
+    // outputs of windows 1 .. MAX_WINDOWS-1 of a multi-window close (window 0
+    // uses the buffers above), allocated on first use
+    struct Win {
+        uint16_t *cnt = nullptr;
+        unsigned long long *aat = nullptr;
+        uint32_t *sa_n = nullptr, *sa_x = nullptr, *sa_mask = nullptr;
+        Status *status = nullptr;
+        asse_superpoint *csip = nullptr, *report = nullptr;
+    } win[MAX_WINDOWS - 1];
+    uint32_t n_windows = 1, sel = 0;  // windows of the last close, the one the readers return
     int scanned = 0, refreshed = 0, restored = 0, ingested = 0;
     uint32_t scan_kp = 0;
     uint64_t scan_slice = 0;
@@ -155,6 +165,29 @@ ScanOut scan_out(asse_pool *p)
     return o;
 }
 
+// Scan outputs, status and lists of window m of the last close.
+ScanOut scan_out_w(asse_pool *p, uint32_t m)
+{
+    if (m == 0)
+        return scan_out(p);
+    const asse_pool::Win &w = p->win[m - 1];
+    ScanOut o;
+    o.cnt = w.cnt;
+    o.aat = w.aat;
+    o.sa_n = w.sa_n;
+    o.sa_x = w.sa_x;
+    o.sa_mask = w.sa_mask;
+    o.status = w.status;
+    return o;
+}
+
+asse_superpoint *list_w(asse_pool *p, uint32_t m, bool reported)
+{
+    if (m == 0)
+        return reported ? p->report : p->csip;
+    return reported ? p->win[m - 1].report : p->win[m - 1].csip;
+}
+
 __global__ void init_pool_kernel(uint32_t *pool, uint64_t nwords, uint32_t Wd, uint32_t words_used,
                                  uint32_t full_word, uint32_t last_word)
 {
@@ -184,7 +217,8 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
         return fail(p, ASSE_EINVAL, "NULL argument");
     if (!p->restored)
         return fail(p, ASSE_ESTATE, "no restore since the last scan");
-    CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaMemcpyAsync(p->status_host, scan_out_w(p, p->sel).status, sizeof(Status), cudaMemcpyDeviceToHost,
+                          p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     const Status st = *p->status_host;
     if (st.error)
@@ -202,7 +236,7 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
     if (m > 0) {
         if (!out)
             return fail(p, ASSE_EINVAL, "out is NULL");
-        CK(p, cudaMemcpyAsync(out, reported ? p->report : p->csip, m * sizeof(asse_superpoint),
+        CK(p, cudaMemcpyAsync(out, list_w(p, p->sel, reported), m * sizeof(asse_superpoint),
                               where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
         if (where != ASSE_DEVICE)
             CK(p, cudaStreamSynchronize(p->stream));
@@ -229,6 +263,10 @@ void free_all(asse_pool *p)
     cudaFree(p->stage[1]);
     cudaFree(p->q_aips);
     cudaFree(p->q_out);
+    for (auto &w : p->win)
+        for (void *ptr : {(void *)w.cnt, (void *)w.aat, (void *)w.sa_n, (void *)w.sa_x, (void *)w.sa_mask,
+                          (void *)w.status, (void *)w.csip, (void *)w.report})
+            cudaFree(ptr);
     if (p->status_host)
         cudaFreeHost(p->status_host);
     for (int i = 0; i < 2; i++) {
@@ -271,6 +309,8 @@ int pool_enqueue_close(asse_pool *p, uint32_t kp)
 
 void pool_after_close(asse_pool *p, uint32_t kp)
 {
+    p->n_windows = 1;
+    p->sel = 0;
     p->scanned = 1;
     p->restored = 1;
     p->refreshed = 1;
@@ -557,6 +597,8 @@ int asse_scan(asse_pool *p, uint32_t kp)
     if (int rc = reset_close_state(p))
         return rc;
     CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    p->n_windows = 1;
+    p->sel = 0;
     p->scanned = 1;
     p->refreshed = 0;
     p->restored = 0;
@@ -598,6 +640,72 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
     if (int rc = pool_enqueue_close(p, kp))
         return rc;
     pool_after_close(p, kp);
+    return ASSE_OK;
+}
+
+int asse_close_slice_multi(asse_pool *p, const uint32_t *kps, uint32_t n_windows)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (!kps || n_windows < 1 || n_windows > (uint32_t)MAX_WINDOWS)
+        return fail(p, ASSE_EINVAL, "need kps and 1 <= n_windows <= ASSE_MAX_WINDOWS");
+    for (uint32_t m = 0; m < n_windows; m++)
+        if (int rc = check_kp(p, kps[m]))
+            return rc;
+    // outputs of the extra windows, on first use
+    const uint64_t n_atv = (uint64_t)p->cfg.r << p->P.E_log2;
+    const size_t nseg = (size_t)p->cfg.r * p->P.nf;
+    for (uint32_t m = 1; m < n_windows; m++) {
+        asse_pool::Win &w = p->win[m - 1];
+        if (w.cnt)
+            continue;
+        cudaError_t e = cudaSuccess;
+        auto alloc = [&](void **ptr, size_t bytes) {
+            if (e == cudaSuccess)
+                e = cudaMalloc(ptr, bytes);
+        };
+        alloc((void **)&w.cnt, n_atv * sizeof(uint16_t));
+        alloc((void **)&w.aat, nseg * sizeof(unsigned long long));
+        alloc((void **)&w.sa_n, nseg * sizeof(uint32_t));
+        alloc((void **)&w.sa_x, n_atv * sizeof(uint32_t));
+        alloc((void **)&w.sa_mask, n_atv * p->P.mw * sizeof(uint32_t));
+        alloc((void **)&w.status, sizeof(Status));
+        alloc((void **)&w.csip, p->out_cap * sizeof(asse_superpoint));
+        alloc((void **)&w.report, p->out_cap * sizeof(asse_superpoint));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (void *ptr : {(void *)w.cnt, (void *)w.aat, (void *)w.sa_n, (void *)w.sa_x, (void *)w.sa_mask,
+                              (void *)w.status, (void *)w.csip, (void *)w.report})
+                cudaFree(ptr);
+            w = asse_pool::Win();
+            return e == cudaErrorMemoryAllocation ? fail(p, ASSE_ENOMEM, "window outputs: device allocation failed")
+                                                  : cuda_fail(p, e, "window outputs");
+        }
+    }
+    ScanWindows W{};
+    W.n = n_windows;
+    for (uint32_t m = 0; m < n_windows; m++) {
+        W.kp[m] = kps[m];
+        W.o[m] = scan_out_w(p, m);
+        CK(p, launch_reset(W.o[m].aat, W.o[m].sa_n, p->cfg.r * p->P.nf, W.o[m].status, p->stream, &p->launches));
+    }
+    CK(p, launch_scan_windows(p->P, p->w, p->pool, W, p->ctl, p->sms, p->stream, &p->launches));
+    for (uint32_t m = 0; m < n_windows; m++)
+        CK(p, launch_restore(p->P, W.o[m], p->scratch, p->cap, list_w(p, m, false), list_w(p, m, true), p->out_cap,
+                             p->stream, &p->launches));
+    CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
+    pool_after_close(p, kps[0]);
+    p->n_windows = n_windows;
+    return ASSE_OK;
+}
+
+int asse_select_window(asse_pool *p, uint32_t window)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (window >= p->n_windows)
+        return fail(p, ASSE_EINVAL, "window index beyond the windows of the last close");
+    p->sel = window;
     return ASSE_OK;
 }
 
@@ -652,7 +760,7 @@ int asse_counts(asse_pool *p, uint16_t *out, int where)
     if (!p->scanned)
         return fail(p, ASSE_ESTATE, "no scan");
     const size_t bytes = ((size_t)p->cfg.r << p->P.E_log2) * sizeof(uint16_t);
-    CK(p, cudaMemcpyAsync(out, p->cnt, bytes,
+    CK(p, cudaMemcpyAsync(out, scan_out_w(p, p->sel).cnt, bytes,
                           where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
     if (where != ASSE_DEVICE)
         CK(p, cudaStreamSynchronize(p->stream));
@@ -665,8 +773,8 @@ int asse_loads(asse_pool *p, uint64_t *out)
         return fail(p, ASSE_EINVAL, "NULL argument");
     if (!p->scanned)
         return fail(p, ASSE_ESTATE, "no scan");
-    CK(p, cudaMemcpyAsync(out, p->aat, (size_t)p->cfg.r * p->P.nf * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                          p->stream));
+    CK(p, cudaMemcpyAsync(out, scan_out_w(p, p->sel).aat, (size_t)p->cfg.r * p->P.nf * sizeof(uint64_t),
+                          cudaMemcpyDeviceToHost, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     return ASSE_OK;
 }

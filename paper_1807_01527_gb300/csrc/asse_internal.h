@@ -66,7 +66,8 @@ struct ScanGeom {
     uint32_t tile_offset; // byte offset of the tile buffers in dynamic shared memory
     uint32_t smem;        // dynamic shared memory bytes
 };
-ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit);
+// nw windows: the count ranges of every window are kept in shared memory
+ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, uint32_t nw, size_t smem_limit);
 
 // Slice-dependent launch arguments, kept in device memory so that a captured
 // CUDA graph replays unchanged from slice to slice: the open slice, the ACT
@@ -143,6 +144,16 @@ cudaError_t launch_reset(unsigned long long *aat, uint32_t *sa_n, uint32_t nseg,
                          uint64_t *launches);
 cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
                         const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches);
+// Several windows k' (Sec. 3: the same ATs answer every k' <= k) counted in
+// one pass over the pool, each into its own outputs; fused refresh.
+constexpr int MAX_WINDOWS = ASSE_MAX_WINDOWS;
+struct ScanWindows {
+    uint32_t n;
+    uint32_t kp[MAX_WINDOWS];
+    ScanOut o[MAX_WINDOWS];
+};
+cudaError_t launch_scan_windows(const Params &P, uint32_t w, uint32_t *pool, const ScanWindows &W,
+                                const SliceCtl *ctl, int sms, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const SliceCtl *ctl, int sms, cudaStream_t s,
                            uint64_t *launches);
 cudaError_t launch_restore(const Params &P, const ScanOut &o, Tuple *scratch, uint32_t cap, asse_superpoint *csip,

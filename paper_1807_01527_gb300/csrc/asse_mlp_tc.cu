@@ -14,12 +14,12 @@
 // loads from the row-major feature matrix, out-of-range rows filled with
 // zeros) and the matching 16 columns of W1 (one bulk copy, L2-resident).
 //
-// Warp roles (12 warps): warp 0 issues the copies, warp 1 owns the tensor
-// memory and one of its lanes issues every MMA, warps 4..11 are the epilogue
-// (two warpgroups; warp w reads accumulator lanes 32 (w mod 4) ..; warpgroup
-// h takes columns 128 h .. 128 h + 127 of each accumulator).  The MMA of
-// layer 2 of one tile and layer 1 of the next run back to back while the
-// epilogue drains acc2.
+// Warp roles (20 warps): warp 0 issues the copies, warp 1 owns the tensor
+// memory and one of its lanes issues every MMA, warps 4..19 are the epilogue
+// (four warpgroups; warp w reads accumulator lanes 32 (w mod 4) ..; warpgroup
+// h takes columns 64 h .. 64 h + 63 of each accumulator).  The MMA of layer 2
+// of one tile and layer 1 of the next run back to back while the epilogue
+// drains acc2.
 //
 // Shared-memory operand layouts (no swizzle, K-major core matrices of 8 rows
 // x 16 bytes; LBO = byte distance of core matrices adjacent in K, SBO = in
@@ -53,9 +53,11 @@ constexpr int HID = ASSE_HID;
 constexpr int TM = 128;                         // rows per tile (MMA M)
 constexpr int K1_STEPS = FEAT / 16;             // 5
 constexpr int K2_STEPS = HID / 16;              // 16
-constexpr int THREADS = 384;
 constexpr int EPI_WARP0 = 4;
-constexpr int EPI_THREADS = 256;
+constexpr int EPI_WARPS = 16;                   // four warpgroups, 64 accumulator columns each
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;
+constexpr int EPI_COLS = HID / (EPI_WARPS / 4);  // 64
 
 // parameter offsets (fp32 vector, asse_learn.h order)
 constexpr size_t P_B1 = (size_t)HID * FEAT;
@@ -71,8 +73,8 @@ constexpr uint32_t SM_W1 = SM_X + 2 * X_STAGE;  // 2 stages of W1
 constexpr uint32_t SM_H1 = SM_W1 + 2 * W1_STAGE;
 constexpr uint32_t SM_W2 = SM_H1 + TM * HID * 2;
 constexpr uint32_t SM_BIAS = SM_W2 + HID * HID * 2;  // b1, b2, w3 (fp32)
-constexpr uint32_t SM_RED = SM_BIAS + 3 * HID * 4;   // [2][128] fp32
-constexpr uint32_t SM_BAR = SM_RED + 2 * TM * 4;
+constexpr uint32_t SM_RED = SM_BIAS + 3 * HID * 4;   // [2][4][128] fp32 partial dots
+constexpr uint32_t SM_BAR = SM_RED + 2 * 4 * TM * 4;
 constexpr int NBAR = 11;
 constexpr uint32_t SM_MISC = SM_BAR + NBAR * 8;      // tmem base, abort flag
 constexpr uint32_t SM_TOTAL = SM_MISC + 16;
@@ -124,22 +126,18 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive accumulator columns of this thread's lane, waited for.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+// 64 consecutive accumulator columns of this thread's lane, waited for.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v)
 {
-    uint32_t r[32];
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; i++)
+    for (int i = 0; i < 64; i++)
         v[i] = __uint_as_float(r[i]);
 }
 
@@ -225,7 +223,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(&bar[B_ACC2_EMPTY], EPI_THREADS);
         mbar_init(&bar[B_W], 1);
         mbar_init(&bar[B_FINAL], 1);
-        mbar_init(&bar[B_RED], EPI_THREADS / 2);
+        mbar_init(&bar[B_RED], EPI_THREADS - EPI_THREADS / 4);
         tmem_slot[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -328,8 +326,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp >= EPI_WARP0) {
         // ------------------------------------------------ epilogue
-        const int ew = warp - EPI_WARP0;
-        const int half = ew >> 2;             // column half of the accumulators
+        const int quarter = (warp - EPI_WARP0) >> 2;  // accumulator columns 64 quarter .. + 63
+        const int c0 = quarter * EPI_COLS;
         const int row = (warp & 3) * 32 + lane;
         const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
         uint8_t *h1 = sm + SM_H1 + (row >> 3) * 4096 + (row & 7) * 16;
@@ -340,19 +338,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!__all_sync(FULL_MASK, wait_or_abort(&bar[B_ACC1_FULL], it & 1u, abort_flag)))
                 break;
             tc_fence_after();
-#pragma unroll 1
-            for (int cc = 0; cc < 4; cc++) {
-                const int c0 = half * 128 + cc * 32;
-                float v[32];
-                tmem_ld32(tmem + lane_addr + c0, v);
+            {
+                float v[64];
+                tmem_ld64(tmem + lane_addr + c0, v);
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
+                for (int q = 0; q < 8; q++) {
+                    const float4 ba = *reinterpret_cast<const float4 *>(b1s + c0 + q * 8);
+                    const float4 bb = *reinterpret_cast<const float4 *>(b1s + c0 + q * 8 + 4);
                     uint4 o;
-                    const float *bb = b1s + c0 + q * 8;
-                    o.x = pack_bf16x2(fmaxf(v[q * 8 + 0] + bb[0], 0.0f), fmaxf(v[q * 8 + 1] + bb[1], 0.0f));
-                    o.y = pack_bf16x2(fmaxf(v[q * 8 + 2] + bb[2], 0.0f), fmaxf(v[q * 8 + 3] + bb[3], 0.0f));
-                    o.z = pack_bf16x2(fmaxf(v[q * 8 + 4] + bb[4], 0.0f), fmaxf(v[q * 8 + 5] + bb[5], 0.0f));
-                    o.w = pack_bf16x2(fmaxf(v[q * 8 + 6] + bb[6], 0.0f), fmaxf(v[q * 8 + 7] + bb[7], 0.0f));
+                    o.x = pack_bf16x2(fmaxf(v[q * 8 + 0] + ba.x, 0.0f), fmaxf(v[q * 8 + 1] + ba.y, 0.0f));
+                    o.y = pack_bf16x2(fmaxf(v[q * 8 + 2] + ba.z, 0.0f), fmaxf(v[q * 8 + 3] + ba.w, 0.0f));
+                    o.z = pack_bf16x2(fmaxf(v[q * 8 + 4] + bb.x, 0.0f), fmaxf(v[q * 8 + 5] + bb.y, 0.0f));
+                    o.w = pack_bf16x2(fmaxf(v[q * 8 + 6] + bb.z, 0.0f), fmaxf(v[q * 8 + 7] + bb.w, 0.0f));
                     *reinterpret_cast<uint4 *>(h1 + ((c0 >> 3) + q) * 128) = o;
                 }
             }
@@ -363,30 +360,32 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             tc_fence_after();
             float dot = 0.0f;
-#pragma unroll 1
-            for (int cc = 0; cc < 4; cc++) {
-                const int c0 = half * 128 + cc * 32;
-                float v[32];
-                tmem_ld32(tmem + lane_addr + ACC2_COL + c0, v);
+            {
+                float v[64];
+                tmem_ld64(tmem + lane_addr + ACC2_COL + c0, v);
+                tc_fence_before();
+                mbar_arrive(&bar[B_ACC2_EMPTY]);  // acc2 is in registers: the next tile's layer 2 may start
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(v[i] + b2s[c0 + i], 0.0f)));
-                    dot = fmaf(h, w3s[c0 + i], dot);
+                for (int q = 0; q < 16; q++) {
+                    const float4 bq = *reinterpret_cast<const float4 *>(b2s + c0 + q * 4);
+                    const float4 wq = *reinterpret_cast<const float4 *>(w3s + c0 + q * 4);
+                    dot = fmaf(__bfloat162float(__float2bfloat16_rn(fmaxf(v[q * 4 + 0] + bq.x, 0.0f))), wq.x, dot);
+                    dot = fmaf(__bfloat162float(__float2bfloat16_rn(fmaxf(v[q * 4 + 1] + bq.y, 0.0f))), wq.y, dot);
+                    dot = fmaf(__bfloat162float(__float2bfloat16_rn(fmaxf(v[q * 4 + 2] + bq.z, 0.0f))), wq.z, dot);
+                    dot = fmaf(__bfloat162float(__float2bfloat16_rn(fmaxf(v[q * 4 + 3] + bq.w, 0.0f))), wq.w, dot);
                 }
             }
-            tc_fence_before();
-            mbar_arrive(&bar[B_ACC2_EMPTY]);
-            // the second column half hands its partial sums to the first
-            float *r = red + (it & 1u) * TM;
-            if (half == 1) {
-                r[row] = dot;
+            // quarters 1..3 hand their partial sums to quarter 0
+            float *r = red + (it & 1u) * 4 * TM;
+            if (quarter > 0) {
+                r[quarter * TM + row] = dot;
                 mbar_arrive(&bar[B_RED]);
             } else {
                 if (!__all_sync(FULL_MASK, wait_or_abort(&bar[B_RED], it & 1u, abort_flag)))
                     break;
                 const uint32_t m = tile * TM + row;
                 if (m < n)
-                    y[m] = (dot + r[row]) + b3;
+                    y[m] = (((dot + r[TM + row]) + r[2 * TM + row]) + r[3 * TM + row]) + b3;
             }
         }
     }

@@ -223,10 +223,11 @@ __device__ __forceinline__ uint32_t decay_swar(uint32_t w)
 
 // ---------------------------------------------------------------- scan kernel
 
-template <int WB, bool FUSE>
-__global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_t *pool, uint32_t kp,
-                                                               const SliceCtl *ctl, ScanOut o, uint32_t total_atv,
-                                                               ScanGeom G)
+// NW: the most windows this instantiation counts (1, or MAX_WINDOWS for the
+// multi-window close, which runs W.n <= NW of them).
+template <int WB, bool FUSE, int NW>
+__global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_t *pool, const ScanWindows W,
+                                                               const SliceCtl *ctl, uint32_t total_atv, ScanGeom G)
 {
     const uint32_t c0 = ctl->c0;
     const Refresh R = ctl->R;
@@ -234,21 +235,24 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     // The count ranges of word q sit in two 16-byte halves at index q + (the
     // segment of q): the lanes of one warp read positions one segment apart,
     // and the skew puts those reads in distinct bank groups.
+    // Window m's table starts at m * n_cd.
+    const uint32_t nw = NW == 1 ? 1u : W.n;
     const uint32_t n_cd = P.Wd + G.lpa;
-    uint4 *cd_lo = reinterpret_cast<uint4 *>(smem);                          // [Wd + lpa]
-    uint4 *cd_hi = cd_lo + n_cd;                                             // [Wd + lpa]
-    RangeDesc *rdesc = reinterpret_cast<RangeDesc *>(cd_hi + n_cd);          // [Wd]
+    uint4 *cd_lo = reinterpret_cast<uint4 *>(smem);                          // [nw][Wd + lpa]
+    uint4 *cd_hi = cd_lo + nw * n_cd;                                        // [nw][Wd + lpa]
+    RangeDesc *rdesc = reinterpret_cast<RangeDesc *>(cd_hi + nw * n_cd);     // [Wd]
     uint64_t *mbar = reinterpret_cast<uint64_t *>(rdesc + P.Wd);             // [warps][2]
     uint32_t *maskbuf = reinterpret_cast<uint32_t *>(mbar + 2 * G.warps);    // [warps][mw]
     uint32_t *tiles = reinterpret_cast<uint32_t *>(smem + G.tile_offset);    // [warps][2][tile_words]
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x) {
-        const RangeDesc d = count_desc<WB>(P, q, c0, kp);
-        const uint32_t x = q + q / G.wseg;
+    for (uint32_t e = threadIdx.x; e < nw * P.Wd; e += blockDim.x) {
+        const uint32_t m = e / P.Wd, q = e - m * P.Wd;
+        const RangeDesc d = count_desc<WB>(P, q, c0, W.kp[m]);
+        const uint32_t x = m * n_cd + q + q / G.wseg;
         cd_lo[x] = make_uint4(d.lo1e, d.hih1e, d.lo1o, d.hih1o);
         cd_hi[x] = make_uint4(d.lo2e, d.hih2e, d.lo2o, d.hih2o);
-        if (FUSE)
+        if (FUSE && m == 0)
             rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
     }
     if (warp < G.warps && lane == 0) {
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
             // the copy did not land: flag it, give the other copy in flight a
             // bounded chance to finish, and leave
             if (lane == 0)
-                atomicExch(&o.status->error, 1u);
+                for (uint32_t m = 0; m < nw; m++)
+                    atomicExch(&W.o[m].status->error, 1u);
             if (next < ntiles)
                 mbar_wait(bar[b ^ 1], parity[b ^ 1]);
             return;
@@ -305,69 +310,88 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
         const uint32_t n_atv = min(G.apt, total_atv - atv0);
         const bool mine = a < n_atv;
         uint32_t *row = tile_buf[b] + lane * G.seg_stride;
-        uint32_t cnt = 0;
+        uint32_t cnt[NW];
+#pragma unroll
+        for (int m = 0; m < NW; m++)
+            cnt[m] = 0;
         if (mine) {
 #pragma unroll 2
             for (uint32_t i = 0; i < G.wseg; i += 4) {
                 const uint4 x = *reinterpret_cast<const uint4 *>(row + i);
                 const uint32_t q = q_first + i;
-                const uint32_t xq = q + part;
-                cnt += count_word<WB>(x.x, load_desc(cd_lo, cd_hi, xq)) +
-                       count_word<WB>(x.y, load_desc(cd_lo, cd_hi, xq + 1)) +
-                       count_word<WB>(x.z, load_desc(cd_lo, cd_hi, xq + 2)) +
-                       count_word<WB>(x.w, load_desc(cd_lo, cd_hi, xq + 3));
-            }
-        }
-        for (uint32_t off = 1; off < G.lpa; off <<= 1)
-            cnt += __shfl_xor_sync(FULL_MASK, cnt, off);
-
-        // one lane per ATV: count, row-frame load, super test
-        const uint32_t atv = atv0 + a;
-        const bool head = mine && part == 0;
-        const uint32_t sg = head ? atv >> P.c : 0xffffffffu;  // row * 2^u + frame
-        if (head)
-            o.cnt[atv] = (uint16_t)cnt;
-        {
-            const unsigned grp = __match_any_sync(FULL_MASK, sg);
-            const uint32_t s = __reduce_add_sync(grp, head ? cnt : 0u);
-            if (head && (uint32_t)(__ffs(grp) - 1) == lane && s)
-                atomicAdd(&o.aat[sg], (unsigned long long)s);
-        }
-        const bool sup = head && cnt >= P.T;
-        uint32_t slot = 0;
-        if (sup) {
-            slot = atomicAdd(&o.sa_n[sg], 1u);
-            o.sa_x[(size_t)sg * cols + slot] = atv & P.cmask;
-        }
-        unsigned sbits = __ballot_sync(FULL_MASK, sup);
-        while (sbits) {
-            // the g-bit active mask of one super ATV, for Algorithm 5
-            const uint32_t hl = __ffs(sbits) - 1;
-            sbits &= sbits - 1;
-            const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
-            const uint32_t a_s = hl / G.lpa;
-            const uint32_t sg_a = (atv0 + a_s) >> P.c;
-            for (uint32_t m = lane; m < P.mw; m += 32)
-                my_mask[m] = 0;
-            __syncwarp();
-            if (a == a_s) {
-                constexpr uint32_t F = 32 / WB;
-                for (uint32_t i = 0; i < G.wseg; i++) {
-                    const uint32_t q = q_first + i;
-                    const uint32_t am = field_bits<WB>(row[i], load_desc(cd_lo, cd_hi, q + part));
-                    if (am) {
-                        const uint32_t pos = q * F, off = pos & 31;
-                        atomicOr(&my_mask[pos >> 5], am << off);
-                        if (off + F > 32 && (am >> (32 - off)))
-                            atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
+#pragma unroll
+                for (int m = 0; m < NW; m++) {
+                    if (m < (int)nw) {
+                        const uint32_t xq = m * n_cd + q + part;
+                        cnt[m] += count_word<WB>(x.x, load_desc(cd_lo, cd_hi, xq)) +
+                                  count_word<WB>(x.y, load_desc(cd_lo, cd_hi, xq + 1)) +
+                                  count_word<WB>(x.z, load_desc(cd_lo, cd_hi, xq + 2)) +
+                                  count_word<WB>(x.w, load_desc(cd_lo, cd_hi, xq + 3));
                     }
                 }
             }
-            __syncwarp();
-            uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
-            for (uint32_t m = lane; m < P.mw; m += 32)
-                dst[m] = my_mask[m];
-            __syncwarp();
+        }
+        const uint32_t atv = atv0 + a;
+        const bool head = mine && part == 0;
+        const uint32_t sg = head ? atv >> P.c : 0xffffffffu;  // row * 2^u + frame
+        const unsigned grp = __match_any_sync(FULL_MASK, sg);
+#pragma unroll 1
+        for (uint32_t m = 0; m < nw; m++) {
+            const ScanOut &o = W.o[m];
+            uint32_t c = NW == 1 ? cnt[0] : 0u;
+            if (NW > 1) {
+#pragma unroll
+                for (int mm = 0; mm < NW; mm++)
+                    if ((uint32_t)mm == m)
+                        c = cnt[mm];
+            }
+            for (uint32_t off = 1; off < G.lpa; off <<= 1)
+                c += __shfl_xor_sync(FULL_MASK, c, off);
+
+            // one lane per ATV: count, row-frame load, super test
+            if (head)
+                o.cnt[atv] = (uint16_t)c;
+            {
+                const uint32_t s = __reduce_add_sync(grp, head ? c : 0u);
+                if (head && (uint32_t)(__ffs(grp) - 1) == lane && s)
+                    atomicAdd(&o.aat[sg], (unsigned long long)s);
+            }
+            const bool sup = head && c >= P.T;
+            uint32_t slot = 0;
+            if (sup) {
+                slot = atomicAdd(&o.sa_n[sg], 1u);
+                o.sa_x[(size_t)sg * cols + slot] = atv & P.cmask;
+            }
+            unsigned sbits = __ballot_sync(FULL_MASK, sup);
+            while (sbits) {
+                // the g-bit active mask of one super ATV, for Algorithm 5
+                const uint32_t hl = __ffs(sbits) - 1;
+                sbits &= sbits - 1;
+                const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
+                const uint32_t a_s = hl / G.lpa;
+                const uint32_t sg_a = (atv0 + a_s) >> P.c;
+                for (uint32_t k = lane; k < P.mw; k += 32)
+                    my_mask[k] = 0;
+                __syncwarp();
+                if (a == a_s) {
+                    constexpr uint32_t F = 32 / WB;
+                    for (uint32_t i = 0; i < G.wseg; i++) {
+                        const uint32_t q = q_first + i;
+                        const uint32_t am = field_bits<WB>(row[i], load_desc(cd_lo, cd_hi, m * n_cd + q + part));
+                        if (am) {
+                            const uint32_t pos = q * F, off = pos & 31;
+                            atomicOr(&my_mask[pos >> 5], am << off);
+                            if (off + F > 32 && (am >> (32 - off)))
+                                atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
+                        }
+                    }
+                }
+                __syncwarp();
+                uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
+                for (uint32_t k = lane; k < P.mw; k += 32)
+                    dst[k] = my_mask[k];
+                __syncwarp();
+            }
         }
 
         if (FUSE && !P.ace) {
@@ -472,7 +496,7 @@ __global__ void __launch_bounds__(256) ace_decay_kernel(uint4 *pool, uint64_t nv
 // Tile geometry of the scan for ATVs of Wd words: lanes per ATV (so a lane
 // holds at most 48 words where Wd allows), the shared-memory stride of a lane's segment (an odd
 // number of 16-byte units) and how many warps fit the shared memory.
-ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit)
+ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, uint32_t nw, size_t smem_limit)
 {
     ScanGeom G{};
     G.lpa = 1;
@@ -485,7 +509,7 @@ ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit)
     G.seg_stride = units * 4;
     G.apt = 32 / G.lpa;
     G.tile_words = 32 * G.seg_stride;
-    const size_t fixed = (size_t)(Wd + G.lpa) * 2 * sizeof(uint4) + (size_t)Wd * sizeof(RangeDesc);
+    const size_t fixed = (size_t)nw * (Wd + G.lpa) * 2 * sizeof(uint4) + (size_t)Wd * sizeof(RangeDesc);
     auto head = [&](uint32_t warps) {
         const size_t h = fixed + 2 * warps * sizeof(uint64_t) + (size_t)warps * mw * 4;
         return (h + 127) / 128 * 128;
@@ -498,24 +522,52 @@ ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, size_t smem_limit)
     return G;
 }
 
-cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
-                        const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches)
+namespace {
+
+template <int NW>
+cudaError_t launch_scan_nw(const Params &P, uint32_t w, uint32_t *pool, const ScanWindows &W, bool fuse,
+                           const SliceCtl *ctl, int sms, cudaStream_t s)
 {
     const uint32_t total = P.r << P.E_log2;
-    const ScanGeom G = scan_geometry(P.Wd, P.mw, 200 * 1024);
+    const ScanGeom G = scan_geometry(P.Wd, P.mw, W.n, 200 * 1024);
     const uint32_t ntiles = (total + G.apt - 1) / G.apt;
-    *launches += 1;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        auto kern = fuse ? scan_kernel<WB, true> : scan_kernel<WB, false>;
+        auto kern = scan_kernel<WB, true, NW>;
+        if constexpr (NW == 1) {
+            if (!fuse)
+                kern = scan_kernel<WB, false, 1>;
+        }
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem);
         if (e != cudaSuccess)
             return e;
         const uint64_t want = (ntiles + G.warps - 1) / G.warps;
         const unsigned grid = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
-        kern<<<grid, SCAN_THREADS, G.smem, s>>>(P, pool, kp, ctl, o, total, G);
+        kern<<<grid, SCAN_THREADS, G.smem, s>>>(P, pool, W, ctl, total, G);
         return cudaGetLastError();
     });
+}
+
+}  // namespace
+
+cudaError_t launch_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
+                        const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches)
+{
+    ScanWindows W{};
+    W.n = 1;
+    W.kp[0] = kp;
+    W.o[0] = o;
+    *launches += 1;
+    return launch_scan_nw<1>(P, w, pool, W, fuse, ctl, sms, s);
+}
+
+cudaError_t launch_scan_windows(const Params &P, uint32_t w, uint32_t *pool, const ScanWindows &W,
+                                const SliceCtl *ctl, int sms, cudaStream_t s, uint64_t *launches)
+{
+    if (W.n < 1 || W.n > (uint32_t)MAX_WINDOWS)
+        return cudaErrorInvalidValue;
+    *launches += 1;
+    return launch_scan_nw<MAX_WINDOWS>(P, w, pool, W, true, ctl, sms, s);
 }
 
 cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const SliceCtl *ctl, int sms, cudaStream_t s,

@@ -222,3 +222,42 @@ def test_link_full_size_three_slices(mods):
         check_close(pool, orc, w.k)
         orc.advance()
         np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+
+
+@pytest.mark.parametrize("k,g,r,c,u,s,counter,n_win", [
+    (6, 150, 4, 9, 2, 7, "at", 3), (10, 211, 4, 9, 2, 7, "at", 4), (5, 77, 5, 7, 1, 6, "ace", 4),
+    (1, 64, 4, 8, 0, 8, "ace", 2), (20, 97, 8, 6, 2, 4, "at", 2)])
+def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
+    """One pass over the pool for several windows k' <= k: every window's
+    counts, loads, candidates and report equal the oracle's close for that
+    window on the same state, and the refreshed state equals the oracle's."""
+    asse, oracle, torch = mods
+    theta = max(4, g // 3)
+    p = _params(k, g, r, c, u, s, theta, seed=3 * k + g)
+    pool = asse.Pool(p, counter=counter, restore_cap=1 << 14)
+    orc = oracle.Oracle.from_params(p, mode=1 if counter == "ace" else 0)
+    heavy = [theta // 2, theta, 2 * theta, 3 * theta]
+    rng = np.random.default_rng(k + 7 * g)
+    for t in range(min(2 * k + 3, 30)):
+        n = int(rng.integers(1, 4000)) | 1
+        pairs = mixed_pairs(k + g + 1, t, n, heavy)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        kps = [k, max(1, k - 2), 1, (k + 1) // 2][:n_win]
+        if t % 4 == 3:
+            kps = kps[::-1]
+        pool.close_slice_multi(kps)
+        for m, kp in enumerate(kps):
+            pool.select_window(m)
+            res = orc.close_report(kp, cap=pool.out_cap, limit_extra=0)
+            np.testing.assert_array_equal(pool.counts(), res["counts"], err_msg=f"t={t} window {m} k'={kp}")
+            np.testing.assert_array_equal(pool.loads(), res["aat"])
+            assert res["n_candidates"] <= pool.cap
+            compare_lists(pool.candidates(), res["candidates"], orc.theta, "csip")
+            compare_lists(pool.report(), [row for row in res["candidates"] if row[1] >= orc.theta], orc.theta,
+                          "report")
+        with pytest.raises(asse.AsseError):
+            pool.select_window(len(kps))
+        orc.advance()
+        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+    pool.close()
