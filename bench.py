@@ -37,7 +37,7 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch on the link
 # workload, from the ncu capture summarised in profiles/ingest_link.md (caches
 # flushed by ncu); None for other workloads or until the current kernel is captured
-INGEST_TRAFFIC_LINK = 202_521_600
+INGEST_TRAFFIC_LINK = 203_198_208
 
 
 def workload_desc(w) -> dict:

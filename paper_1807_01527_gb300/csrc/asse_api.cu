@@ -48,6 +48,11 @@ struct asse_pool {
     uint64_t out_cap = 0;
     Status *status = nullptr;
     Status *status_host = nullptr;
+    // asse_close_slice also copies the status and the head of the report to
+    // pinned host memory, so that reading a short report takes one wait
+    asse_superpoint *report_host = nullptr;
+    uint64_t report_host_cap = 0;
+    int report_host_valid = 0;
     SliceCtl *ctl = nullptr;  // device copy of the slice-dependent launch arguments
     uint32_t *stage[2] = {nullptr, nullptr};
     uint64_t stage_pairs = 0;
@@ -217,8 +222,10 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
         return fail(p, ASSE_EINVAL, "NULL argument");
     if (!p->restored)
         return fail(p, ASSE_ESTATE, "no restore since the last scan");
-    CK(p, cudaMemcpyAsync(p->status_host, scan_out_w(p, p->sel).status, sizeof(Status), cudaMemcpyDeviceToHost,
-                          p->stream));
+    const bool early = reported && where != ASSE_DEVICE && p->report_host_valid && p->sel == 0;
+    if (!early)
+        CK(p, cudaMemcpyAsync(p->status_host, scan_out_w(p, p->sel).status, sizeof(Status), cudaMemcpyDeviceToHost,
+                              p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     const Status st = *p->status_host;
     if (st.error)
@@ -233,7 +240,11 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
     const uint64_t n = reported ? st.n_report : st.n_csip;
     *n_out = n;
     const uint64_t m = n < cap ? n : cap;
-    if (m > 0) {
+    if (m > 0 && early && m <= p->report_host_cap) {
+        if (!out)
+            return fail(p, ASSE_EINVAL, "out is NULL");
+        memcpy(out, p->report_host, m * sizeof(asse_superpoint));
+    } else if (m > 0) {
         if (!out)
             return fail(p, ASSE_EINVAL, "out is NULL");
         CK(p, cudaMemcpyAsync(out, list_w(p, p->sel, reported), m * sizeof(asse_superpoint),
@@ -269,6 +280,8 @@ void free_all(asse_pool *p)
             cudaFree(ptr);
     if (p->status_host)
         cudaFreeHost(p->status_host);
+    if (p->report_host)
+        cudaFreeHost(p->report_host);
     for (int i = 0; i < 2; i++) {
         if (p->copied[i])
             cudaEventDestroy(p->copied[i]);
@@ -287,6 +300,7 @@ int pool_restore_view(asse_pool *p, RestoreView *v)
 {
     if (!p->scanned)
         return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
+    p->report_host_valid = 0;
     v->P = p->P;
     v->o = scan_out(p);
     v->stream = p->stream;
@@ -309,8 +323,10 @@ int pool_enqueue_close(asse_pool *p, uint32_t kp)
 
 void pool_after_close(asse_pool *p, uint32_t kp)
 {
+    p->report_host_valid = 0;
     p->n_windows = 1;
     p->sel = 0;
+    p->report_host_valid = 0;
     p->scanned = 1;
     p->restored = 1;
     p->refreshed = 1;
@@ -474,6 +490,9 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     alloc((void **)&p->stage[1], p->stage_pairs * 8);
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&p->status_host, sizeof(Status));
+    p->report_host_cap = p->out_cap < 4096 ? p->out_cap : 4096;
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&p->report_host, p->report_host_cap * sizeof(asse_superpoint));
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
@@ -599,6 +618,7 @@ int asse_scan(asse_pool *p, uint32_t kp)
     CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     p->n_windows = 1;
     p->sel = 0;
+    p->report_host_valid = 0;
     p->scanned = 1;
     p->refreshed = 0;
     p->restored = 0;
@@ -614,6 +634,7 @@ int asse_restore(asse_pool *p)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (!p->scanned)
         return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
+    p->report_host_valid = 0;
     CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
                          &p->launches));
     p->restored = 1;
@@ -640,6 +661,10 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
     if (int rc = pool_enqueue_close(p, kp))
         return rc;
     pool_after_close(p, kp);
+    CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaMemcpyAsync(p->report_host, p->report, p->report_host_cap * sizeof(asse_superpoint),
+                          cudaMemcpyDeviceToHost, p->stream));
+    p->report_host_valid = 1;
     return ASSE_OK;
 }
 
@@ -836,6 +861,7 @@ int asse_load(asse_pool *p, const void *src, uint64_t n)
 {
     if (!p || !src)
         return fail(p, ASSE_EINVAL, "NULL argument");
+    p->report_host_valid = 0;
     SnapHeader h;
     if (n < sizeof h)
         return fail(p, ASSE_EINVAL, "image too small");

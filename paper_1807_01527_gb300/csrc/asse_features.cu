@@ -1,0 +1,100 @@
+// Feature rows of every ATV of a pool (asse_features, include/asse_learn.h).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/asse_learn.h"
+#include "asse_features.cuh"
+
+namespace asse {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int FEAT = ASSE_FEAT;
+
+constexpr int FEAT_WARPS = 8;
+
+// M: words per lane, the smallest of 4, 8, 16 that holds the ATV.
+template <int WB, int M>
+__global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, const uint32_t *pool, uint32_t c0,
+                                                                   uint32_t kp, const unsigned long long *aat, bf16 *x,
+                                                                   uint32_t total_atv)
+{
+    extern __shared__ uint32_t fsm[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint16_t *hist = reinterpret_cast<uint16_t *>(fsm + warp * HIST_WORDS);
+    // load features of every (row, frame), then UP and mean P of every frame,
+    // once per block (FP64, then stored as FP32)
+    float *ltab = reinterpret_cast<float *>(fsm + FEAT_WARPS * HIST_WORDS);
+    uint8_t *act_tab = reinterpret_cast<uint8_t *>(ltab + (P.r + 2) * P.nf);  // [g]: ACT of each AT's block
+    for (uint32_t h = threadIdx.x; h < P.g; h += blockDim.x)
+        act_tab[h] = (uint8_t)act_of(P, c0, act_block(P, h));
+    const double denom = (double)P.g * (double)(P.cmask + 1);
+    for (uint32_t frame = threadIdx.x; frame < P.nf; frame += blockDim.x) {
+        double up = 1.0, sum = 0.0;
+        for (uint32_t i = 0; i < P.r; i++) {
+            const double pi = (double)aat[(size_t)i * P.nf + frame] / denom;
+            up *= pi;
+            sum += pi;
+            ltab[i * P.nf + frame] = (float)pi;
+        }
+        ltab[P.r * P.nf + frame] = (float)up;
+        ltab[(P.r + 1) * P.nf + frame] = (float)(sum / P.r);
+    }
+    for (uint32_t i = lane; i < HIST_WORDS; i += 32)
+        fsm[warp * HIST_WORDS + i] = 0;
+    __syncthreads();
+    // all of an ATV's words are loaded at once (one memory latency per ATV)
+    for (uint32_t atv = blockIdx.x * FEAT_WARPS + warp; atv < total_atv; atv += gridDim.x * FEAT_WARPS) {
+        uint32_t wreg[M];
+        load_atv_words<WB, M>(P, pool + (size_t)atv * P.Wd, lane, wreg);
+        const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
+        atv_features<WB, M>(P, wreg, act_tab, kp, ltab[row * P.nf + frame], ltab[P.r * P.nf + frame],
+                         ltab[(P.r + 1) * P.nf + frame], hist, x + (size_t)atv * FEAT, lane, nullptr);
+    }
+}
+
+}  // namespace
+
+}  // namespace asse
+
+using namespace asse;
+
+extern "C" {
+
+int asse_features(asse_pool *pool, uint16_t *x_dev)
+{
+    if (!pool || !x_dev)
+        return pool ? pool_fail(pool, ASSE_EINVAL, "x_dev is NULL") : ASSE_EINVAL;
+    FeatureView v;
+    if (int rc = pool_feature_view(pool, &v))
+        return rc;
+    if (v.kp > 64)
+        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
+    const uint32_t total = v.P.r << v.P.E_log2;
+    cudaError_t e = dispatch_w(v.w, [&](auto wb) {
+        constexpr int WB = decltype(wb)::value;
+        const size_t smem = ((size_t)FEAT_WARPS * HIST_WORDS + (size_t)(v.P.r + 2) * v.P.nf) * sizeof(uint32_t) +
+                            v.P.g;
+        constexpr uint32_t F = 32 / WB;
+        const uint32_t per_lane = ((v.P.g + F - 1) / F + 31) / 32;
+        auto kern = per_lane <= 4 ? features_kernel<WB, 4> : (per_lane <= 8 ? features_kernel<WB, 8>
+                                                                           : features_kernel<WB, 16>);
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e2 != cudaSuccess)
+            return e2;
+        const unsigned grid = (unsigned)v.sms * 4;
+        kern<<<grid, FEAT_WARPS * 32, smem, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
+                                                       reinterpret_cast<bf16 *>(x_dev), total);
+        return cudaGetLastError();
+    });
+    *v.launches += 1;
+    if (e != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, std::string("features launch: ") + cudaGetErrorString(e));
+    return ASSE_OK;
+}
+
+}  // extern "C"

@@ -7,12 +7,13 @@
 // key this block already handled in this launch sets exactly the same r
 // fields to the same values, so it is skipped (SetAT is idempotent within a
 // slice; a key pushed out of the table only means a repeat is processed
-// again).  Unseen keys go to a per-warp queue; every 64 queued keys, each
-// lane takes two, computes f(aip), the frame, the r column indices and the
-// ACT of the AT in registers, issues the r word loads of both together, then
-// sets the r fields; a field that already holds the slice's value costs one
-// load and no atomic.  (A 2-way table of 192 KB removed more repeats but
-// took the L1 cache down to 32 KB and ran twice as long.)
+// again).  Unseen keys go to a per-warp queue; every 32 queued keys, each
+// lane takes one, computes f(aip), the frame, the r column indices and the
+// ACT of the AT in registers, issues the r word loads together, then sets
+// the r fields; a field that already holds the slice's value costs one load
+// and no atomic.  The table is 64 KB: the rest of the SM's 256 KB of L1 /
+// shared memory stays L1 cache, which serves the pool words of keys the
+// table missed (a 128 KB table ran 13 % slower, a 192 KB one 2x slower).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -73,8 +74,8 @@ __device__ __forceinline__ uint32_t *field_word(const Params &P, uint32_t *pool,
 constexpr int INGEST_THREADS = 1024;
 constexpr int INGEST_WARPS = INGEST_THREADS / 32;
 constexpr int INGEST_BLOCKS_PER_SM = 1;
-constexpr uint32_t SEEN_LOG2 = 14;  // 16,384 keys = 128 KB of shared memory per block
-constexpr uint32_t QCAP = 128;      // per-warp queue of new keys (below 64 between rounds, + 64)
+constexpr uint32_t SEEN_LOG2 = 13;  // 8,192 keys = 64 KB of shared memory per block
+constexpr uint32_t QCAP = 96;       // per-warp queue of new keys (below 32 between rounds, + 64)
 constexpr unsigned long long NO_KEY = ~0ull;  // BH values are < 2^16, so never a real key
 
 __device__ __forceinline__ uint32_t seen_slot(uint32_t aip, uint32_t h)
@@ -93,51 +94,38 @@ __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t a
     return false;
 }
 
-// Algorithm 3 for two keys (aip, h = BH(bip)) of this lane, each if its ok
-// flag is set: f(aip), the r column windows, the ACT of AT h, then the r word
-// loads of both keys together and the field sets.
+// Algorithm 3 for one key (aip, h = BH(bip)) of this lane, if ok: f(aip), the
+// r column windows, the ACT of AT h, the r word loads together, then the
+// field sets.
 template <int WB, int R>
-__device__ __forceinline__ void set_keys(const Params &P, uint32_t *pool, uint32_t c0, int r, uint32_t aip0,
-                                         uint32_t h0, bool ok0, uint32_t aip1, uint32_t h1, bool ok1)
+__device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_t c0, int r, uint32_t aip, uint32_t h,
+                                        bool ok)
 {
     constexpr uint32_t F = 32 / WB;
     constexpr uint32_t FM = (1u << WB) - 1;
     constexpr int RM = R ? R : 8;
-    uint64_t LL0 = 0, LL1 = 0;
-    uint32_t z0 = 0, z1 = 0;
-    if (ok0)
-        prep_host(P, aip0, LL0, z0);
-    if (ok1)
-        prep_host(P, aip1, LL1, z1);
-    const uint32_t val0 = P.ace ? P.k : act_of(P, c0, act_block(P, h0));
-    const uint32_t val1 = P.ace ? P.k : act_of(P, c0, act_block(P, h1));
-    const uint32_t q0 = h0 / F, q1 = h1 / F;
-    const uint32_t sh0 = (h0 - q0 * F) * WB, sh1 = (h1 - q1 * F) * WB;
-    uint32_t *a0[RM], *a1[RM];
-    uint32_t o0[RM], o1[RM];
+    if (!ok)
+        return;
+    uint64_t LL;
+    uint32_t z;
+    prep_host(P, aip, LL, z);
+    const uint32_t val = P.ace ? P.k : act_of(P, c0, act_block(P, h));
+    const uint32_t q = h / F;
+    const uint32_t sh = (h - q * F) * WB;
+    uint32_t *a[RM];
+    uint32_t o[RM];
 #pragma unroll
-    for (int i = 0; i < RM; i++) {
-        if (i < r) {
-            a0[i] = field_word(P, pool, i, z0, LL0, q0);
-            a1[i] = field_word(P, pool, i, z1, LL1, q1);
-        }
-    }
+    for (int i = 0; i < RM; i++)
+        if (i < r)
+            a[i] = field_word(P, pool, i, z, LL, q);
 #pragma unroll
-    for (int i = 0; i < RM; i++) {
-        if (i < r) {
-            o0[i] = ok0 ? *a0[i] : 0u;
-            o1[i] = ok1 ? *a1[i] : 0u;
-        }
-    }
+    for (int i = 0; i < RM; i++)
+        if (i < r)
+            o[i] = *a[i];
 #pragma unroll
-    for (int i = 0; i < RM; i++) {
-        if (i < r) {
-            if (ok0)
-                set_field(a0[i], o0[i], sh0, val0, FM);
-            if (ok1)
-                set_field(a1[i], o1[i], sh1, val1, FM);
-        }
-    }
+    for (int i = 0; i < RM; i++)
+        if (i < r)
+            set_field(a[i], o[i], sh, val, FM);
 }
 
 template <int WB, int R>
@@ -160,7 +148,7 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     const int r = R ? R : (int)P.r;
     // Warp-uniform loop: the 32 lanes of a warp take 32 consecutive vectors.
     // Keys the table has not seen go to the warp's queue; whenever it holds
-    // 64 of them, every lane runs Algorithm 3 on two, so the long path runs
+    // 32 of them, every lane runs Algorithm 3 on one, so the long path runs
     // with all lanes busy however many repeats the table removed.
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t base0 = (uint64_t)blockIdx.x * blockDim.x + warp * 32u;
@@ -189,20 +177,19 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
         if (do1)
             queue[qn + __popc(m1 & lt)] = make_uint2(cur.z, h1);
         qn += __popc(m1);
-        if (qn >= 64) {
+        while (qn >= 32) {
             __syncwarp();
-            qn -= 64;
-            const uint2 e0 = queue[qn + lane], e1 = queue[qn + 32 + lane];
+            qn -= 32;
+            const uint2 e = queue[qn + lane];
             __syncwarp();
-            set_keys<WB, R>(P, pool, c0, r, e0.x, e0.y, true, e1.x, e1.y, true);
+            set_key<WB, R>(P, pool, c0, r, e.x, e.y, true);
         }
     }
     __syncwarp();
     if (qn > 0) {
-        const bool ok0 = lane < qn, ok1 = lane + 32 < qn;
-        const uint2 e0 = ok0 ? queue[lane] : make_uint2(0, 0);
-        const uint2 e1 = ok1 ? queue[lane + 32] : make_uint2(0, 0);
-        set_keys<WB, R>(P, pool, c0, r, e0.x, e0.y, ok0, e1.x, e1.y, ok1);
+        const bool ok = lane < qn;
+        const uint2 e = ok ? queue[lane] : make_uint2(0, 0);
+        set_key<WB, R>(P, pool, c0, r, e.x, e.y, ok);
     }
     if (tail != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
         const uint2 pr1 = *tail;

@@ -21,6 +21,7 @@
 
 #include "../../include/asse_learn.h"
 #include "asse_device.cuh"
+#include "asse_features.cuh"
 #include "asse_mlp_tc.h"
 
 using bf16 = __nv_bfloat16;
@@ -40,132 +41,6 @@ constexpr size_t OFF_W3 = OFF_B2 + HID;
 constexpr size_t OFF_B3 = OFF_W3 + HID;
 constexpr size_t NPARAMS = OFF_B3 + 1;
 static_assert(NPARAMS == ASSE_MLP_NPARAMS, "parameter layout");
-
-// ---------------------------------------------------------------- features
-
-// Feature row of one ATV from its packed words (global or shared), computed
-// by one warp: active ATs per age (Algorithm 1 for the latest kp slices) and
-// their total, then the three load features.  Each lane counts ages in its
-// own column of hist ([64][32] 16-bit counters, zero on entry and left zero), so the
-// histogram needs no atomics; the lanes then add up one age row each,
-// reading the row rotated by the age so that no two lanes hit one bank.
-constexpr uint32_t HIST_WORDS = 64 * 32 / 2;  // [64][32] 16-bit counters (a lane counts at most g/32 <= 128)
-
-template <int WB>
-__device__ void atv_features(const Params &P, const uint32_t *words, const uint8_t *act_tab, uint32_t kp, float lp,
-                             float lup, float lmean, uint16_t *hist, bf16 *row, uint32_t lane, uint32_t *cnt_out)
-{
-    constexpr uint32_t F = 32 / WB;
-    constexpr uint32_t FM = (1u << WB) - 1;
-    uint32_t cnt = 0;
-    const uint32_t nw = (P.g + F - 1) / F;
-    for (uint32_t q = lane; q < nw; q += 32) {
-        const uint32_t w = words[q];
-        uint32_t h = q * F;
-#pragma unroll
-        for (uint32_t j = 0; j < F; j++, h++) {
-            if (h >= P.g)
-                break;
-            const uint32_t v = (w >> (j * WB)) & FM;
-            bool active;
-            uint32_t age;
-            if (P.ace) {
-                active = v + kp >= P.k + 1;  // a counter visited age slices ago holds k - age
-                age = P.k - v;
-            } else {
-                uint32_t d = act_tab[h] + P.k2 - v;  // (ACT of the AT's block - v) mod 2k
-                d = d >= P.k2 ? d - P.k2 : d;
-                active = v < P.k2 && d < kp;
-                age = d;
-            }
-            if (active) {
-                cnt++;
-                hist[age * 32 + lane] += 1;
-            }
-        }
-    }
-    cnt = __reduce_add_sync(FULL_MASK, cnt);
-    __syncwarp();
-    uint32_t bins[2] = {0, 0};
-#pragma unroll
-    for (uint32_t t = 0; t < 2; t++) {
-        const uint32_t e = lane + 32 * t;
-        if (e < kp) {
-            uint16_t *hr = hist + e * 32;
-            uint32_t acc = 0;
-            for (uint32_t j = 0; j < 32; j++) {
-                const uint32_t c = (j + e) & 31;
-                acc += hr[c];
-                hr[c] = 0;
-            }
-            bins[t] = acc;
-        }
-    }
-    const float inv_g = 1.0f / (float)P.g;
-#pragma unroll
-    for (uint32_t m = 0; m < (FEAT + 31) / 32; m++) {
-        const uint32_t e = lane + 32 * m;
-        // age e - 1 is held by lane (e - 1) mod 32, in bins[(e - 1) / 32]
-        const uint32_t src = (e + 31) & 31;
-        const uint32_t b0 = __shfl_sync(FULL_MASK, bins[0], src);
-        const uint32_t b1 = __shfl_sync(FULL_MASK, bins[1], src);
-        if (e >= FEAT)
-            continue;
-        float v = 0.0f;
-        if (e == 0)
-            v = (float)cnt * inv_g;
-        else if (e <= 64)
-            v = (float)(e - 1 < 32 ? b0 : b1) * inv_g;
-        else if (e == 65)
-            v = lp;
-        else if (e == 66)
-            v = lup;
-        else if (e == 67)
-            v = lmean;
-        row[e] = __float2bfloat16_rn(v);
-    }
-    if (cnt_out)
-        *cnt_out = cnt;
-    __syncwarp();
-}
-
-constexpr int FEAT_WARPS = 8;
-
-template <int WB>
-__global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, const uint32_t *pool, uint32_t c0,
-                                                                   uint32_t kp, const unsigned long long *aat, bf16 *x,
-                                                                   uint32_t total_atv)
-{
-    extern __shared__ uint32_t fsm[];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint16_t *hist = reinterpret_cast<uint16_t *>(fsm + warp * HIST_WORDS);
-    // load features of every (row, frame), then UP and mean P of every frame,
-    // once per block (FP64, then stored as FP32)
-    float *ltab = reinterpret_cast<float *>(fsm + FEAT_WARPS * HIST_WORDS);
-    uint8_t *act_tab = reinterpret_cast<uint8_t *>(ltab + (P.r + 2) * P.nf);  // [g]: ACT of each AT's block
-    for (uint32_t h = threadIdx.x; h < P.g; h += blockDim.x)
-        act_tab[h] = (uint8_t)act_of(P, c0, act_block(P, h));
-    const double denom = (double)P.g * (double)(P.cmask + 1);
-    for (uint32_t frame = threadIdx.x; frame < P.nf; frame += blockDim.x) {
-        double up = 1.0, sum = 0.0;
-        for (uint32_t i = 0; i < P.r; i++) {
-            const double pi = (double)aat[(size_t)i * P.nf + frame] / denom;
-            up *= pi;
-            sum += pi;
-            ltab[i * P.nf + frame] = (float)pi;
-        }
-        ltab[P.r * P.nf + frame] = (float)up;
-        ltab[(P.r + 1) * P.nf + frame] = (float)(sum / P.r);
-    }
-    for (uint32_t i = lane; i < HIST_WORDS; i += 32)
-        fsm[warp * HIST_WORDS + i] = 0;
-    __syncthreads();
-    for (uint32_t atv = blockIdx.x * FEAT_WARPS + warp; atv < total_atv; atv += gridDim.x * FEAT_WARPS) {
-        const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
-        atv_features<WB>(P, pool + (size_t)atv * P.Wd, act_tab, kp, ltab[row * P.nf + frame], ltab[P.r * P.nf + frame],
-                         ltab[(P.r + 1) * P.nf + frame], hist, x + (size_t)atv * FEAT, lane, nullptr);
-    }
-}
 
 // est[i] = exp(y[i]) where the model is inside its training range (the ATV
 // not saturated and 0 <= y <= max_log_n), else the linear-counting estimate
@@ -294,7 +169,9 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
         if (tid < 32) {
             const float pw = 1.0f - powf(1.0f - pbg, (float)P.k);  // background activity over the window
             uint32_t cnt = 0;
-            atv_features<WB>(P, words, act_tab, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
+            uint32_t wreg[FEAT_MAXM];
+            load_atv_words<WB>(P, words, tid, wreg);
+            atv_features<WB>(P, wreg, act_tab, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
                              tid, &cnt);
             if (tid == 0) {
                 log_n[si] = (float)log((double)card);
@@ -688,35 +565,6 @@ cudaError_t dispatch_w_host(uint32_t w, Fn &&fn)
 }  // namespace
 
 extern "C" {
-
-int asse_features(asse_pool *pool, uint16_t *x_dev)
-{
-    if (!pool || !x_dev)
-        return pool ? pool_fail(pool, ASSE_EINVAL, "x_dev is NULL") : ASSE_EINVAL;
-    FeatureView v;
-    if (int rc = pool_feature_view(pool, &v))
-        return rc;
-    if (v.kp > 64)
-        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
-    const uint32_t total = v.P.r << v.P.E_log2;
-    cudaError_t e = dispatch_w(v.w, [&](auto wb) {
-        constexpr int WB = decltype(wb)::value;
-        const size_t smem = ((size_t)FEAT_WARPS * HIST_WORDS + (size_t)(v.P.r + 2) * v.P.nf) * sizeof(uint32_t) +
-                            v.P.g;
-        cudaError_t e2 = cudaFuncSetAttribute(features_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem);
-        if (e2 != cudaSuccess)
-            return e2;
-        const unsigned grid = (unsigned)v.sms * 4;
-        features_kernel<WB><<<grid, FEAT_WARPS * 32, smem, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
-                                                                       reinterpret_cast<bf16 *>(x_dev), total);
-        return cudaGetLastError();
-    });
-    *v.launches += 1;
-    if (e != cudaSuccess)
-        return pool_fail(pool, ASSE_ECUDA, std::string("features launch: ") + cudaGetErrorString(e));
-    return ASSE_OK;
-}
 
 int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, uint16_t *x_dev, float *est_dev,
                           uint32_t *n_fallback_dev)

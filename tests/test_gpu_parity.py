@@ -261,3 +261,22 @@ def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
         orc.advance()
         np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
     pool.close()
+
+
+def test_long_report_beyond_the_early_copy(mods):
+    """asse_close_slice copies the status and the first 4,096 report entries
+    to pinned host memory so that a short report takes one wait; a report
+    longer than that is read from device memory.  Both against the oracle."""
+    asse, oracle, torch = mods
+    p = _params(2, 64, 4, 10, 8, 5, 6, seed=17)
+    pool = asse.Pool(p, restore_cap=1 << 12)
+    orc = oracle.Oracle.from_params(p)
+    sizes = [40] * 4500
+    for t in range(2):
+        pairs = mixed_pairs(23, t, 300_000, sizes, n_background=0)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        res = check_close(pool, orc, 2)
+        if t == 1:
+            assert len(res["report"]) > 4096, len(res["report"])
+        orc.advance()
