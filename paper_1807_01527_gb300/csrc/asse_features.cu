@@ -28,10 +28,10 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, con
     uint16_t *hist = reinterpret_cast<uint16_t *>(fsm + warp * HIST_WORDS);
     // load features of every (row, frame), then UP and mean P of every frame,
     // once per block (FP64, then stored as FP32)
-    float *ltab = reinterpret_cast<float *>(fsm + FEAT_WARPS * HIST_WORDS);
-    uint8_t *act_tab = reinterpret_cast<uint8_t *>(ltab + (P.r + 2) * P.nf);  // [g]: ACT of each AT's block
-    for (uint32_t h = threadIdx.x; h < P.g; h += blockDim.x)
-        act_tab[h] = (uint8_t)act_of(P, c0, act_block(P, h));
+    RangeDesc *desc = reinterpret_cast<RangeDesc *>(fsm + FEAT_WARPS * HIST_WORDS);  // [Wd]
+    uint32_t *actw = reinterpret_cast<uint32_t *>(desc + P.Wd);                       // [Wd]
+    float *ltab = reinterpret_cast<float *>(actw + P.Wd);                             // [(r + 2) nf]
+    feature_tables<WB>(P, c0, kp, desc, actw);
     const double denom = (double)P.g * (double)(P.cmask + 1);
     for (uint32_t frame = threadIdx.x; frame < P.nf; frame += blockDim.x) {
         double up = 1.0, sum = 0.0;
@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, con
         uint32_t wreg[M];
         load_atv_words<WB, M>(P, pool + (size_t)atv * P.Wd, lane, wreg);
         const uint32_t row = atv >> P.E_log2, frame = (atv & ((1u << P.E_log2) - 1)) >> P.c;
-        atv_features<WB, M>(P, wreg, act_tab, kp, ltab[row * P.nf + frame], ltab[P.r * P.nf + frame],
-                         ltab[(P.r + 1) * P.nf + frame], hist, x + (size_t)atv * FEAT, lane, nullptr);
+        atv_features<WB, M>(P, wreg, desc, actw, kp, ltab[row * P.nf + frame], ltab[P.r * P.nf + frame],
+                            ltab[(P.r + 1) * P.nf + frame], hist, x + (size_t)atv * FEAT, lane, nullptr);
     }
 }
 
@@ -78,7 +78,7 @@ int asse_features(asse_pool *pool, uint16_t *x_dev)
     cudaError_t e = dispatch_w(v.w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         const size_t smem = ((size_t)FEAT_WARPS * HIST_WORDS + (size_t)(v.P.r + 2) * v.P.nf) * sizeof(uint32_t) +
-                            v.P.g;
+                            (size_t)v.P.Wd * (sizeof(RangeDesc) + sizeof(uint32_t));
         constexpr uint32_t F = 32 / WB;
         const uint32_t per_lane = ((v.P.g + F - 1) / F + 31) / 32;
         auto kern = per_lane <= 4 ? features_kernel<WB, 4> : (per_lane <= 8 ? features_kernel<WB, 8>

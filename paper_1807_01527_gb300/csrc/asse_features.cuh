@@ -10,15 +10,18 @@
 
 #include "../../include/asse_learn.h"
 #include "asse_device.cuh"
+#include "asse_swar.cuh"
 
 namespace asse {
 
-
-// Feature row of one ATV from its packed words (global or shared), computed
-// by one warp: active ATs per age (Algorithm 1 for the latest kp slices) and
-// their total, then the three load features.  Each lane counts ages in its
-// own column of hist ([64][32] 16-bit counters, zero on entry and left zero), so the
-// histogram needs no atomics; the lanes then add up one age row each,
+// Feature row of one ATV from its packed words, computed by one warp: active
+// ATs per age (Algorithm 1 for the latest kp slices) and their total, then
+// the three load features.  A word's active fields come from the SWAR range
+// test with the window's per-position ranges (desc); only those fields are
+// visited, their age taken from the ACT of their block (actw: the ACTs of a
+// word's fields packed like the word).  Each lane counts ages in its own
+// column of hist ([64][32] 16-bit counters, zero on entry and left zero), so
+// the histogram needs no atomics; the lanes then add up one age row each,
 // reading the row rotated by the age so that no two lanes hit one bank.
 constexpr uint32_t HIST_WORDS = 64 * 32 / 2;  // [64][32] 16-bit counters (a lane counts at most g/32 <= 128)
 
@@ -37,9 +40,29 @@ __device__ __forceinline__ void load_atv_words(const Params &P, const uint32_t *
     }
 }
 
+// Per-position tables of the window ending at the slice whose block 0 has ACT
+// c0: desc[q] the count ranges of word q, actw[q] the ACT of each of its
+// fields (AT counters; unused for aging counters).  All threads of the block.
+template <int WB>
+__device__ void feature_tables(const Params &P, uint32_t c0, uint32_t kp, RangeDesc *desc, uint32_t *actw)
+{
+    constexpr uint32_t F = 32 / WB;
+    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x) {
+        desc[q] = count_desc<WB>(P, q, c0, kp);
+        uint32_t a = 0;
+        for (uint32_t j = 0; j < F; j++) {
+            const uint32_t h = q * F + j;
+            if (h < P.g)
+                a |= act_of(P, c0, act_block(P, h)) << (j * WB);
+        }
+        actw[q] = a;
+    }
+}
+
 template <int WB, int M = FEAT_MAXM>
-__device__ void atv_features(const Params &P, const uint32_t *wreg, const uint8_t *act_tab, uint32_t kp, float lp,
-                             float lup, float lmean, uint16_t *hist, __nv_bfloat16 *row, uint32_t lane, uint32_t *cnt_out)
+__device__ void atv_features(const Params &P, const uint32_t *wreg, const RangeDesc *desc, const uint32_t *actw,
+                             uint32_t kp, float lp, float lup, float lmean, uint16_t *hist, __nv_bfloat16 *row,
+                             uint32_t lane, uint32_t *cnt_out)
 {
     constexpr uint32_t F = 32 / WB;
     constexpr uint32_t FM = (1u << WB) - 1;
@@ -53,28 +76,24 @@ __device__ void atv_features(const Params &P, const uint32_t *wreg, const uint8_
         if (q >= nw)
             continue;
         const uint32_t w = wreg[m];
-        uint32_t h = q * F;
-#pragma unroll 1
-        for (uint32_t j = 0; j < F; j++, h++) {
-            if (h >= P.g)
-                break;
+        uint32_t am = field_bits<WB>(w, desc[q]);
+        if (am == 0)
+            continue;
+        cnt += __popc(am);
+        const uint32_t acts = actw[q];
+        do {
+            const uint32_t j = __ffs(am) - 1;
+            am &= am - 1;
             const uint32_t v = (w >> (j * WB)) & FM;
-            bool active;
             uint32_t age;
             if (P.ace) {
-                active = v + kp >= P.k + 1;  // a counter visited age slices ago holds k - age
-                age = P.k - v;
+                age = P.k - v;  // a counter visited age slices ago holds k - age
             } else {
-                uint32_t d = act_tab[h] + P.k2 - v;  // (ACT of the AT's block - v) mod 2k
-                d = d >= P.k2 ? d - P.k2 : d;
-                active = v < P.k2 && d < kp;
-                age = d;
+                age = ((acts >> (j * WB)) & FM) + P.k2 - v;  // (ACT of the AT's block - v) mod 2k
+                age = age >= P.k2 ? age - P.k2 : age;
             }
-            if (active) {
-                cnt++;
-                hist[age * 32 + lane] += 1;
-            }
-        }
+            hist[age * 32 + lane] += 1;
+        } while (am);
     }
     cnt = __reduce_add_sync(FULL_MASK, cnt);
     __syncwarp();

@@ -156,8 +156,11 @@ cudaError_t launch_scan_windows(const Params &P, uint32_t w, uint32_t *pool, con
                                 const SliceCtl *ctl, int sms, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_refresh(const Params &P, uint32_t w, uint32_t *pool, const SliceCtl *ctl, int sms, cudaStream_t s,
                            uint64_t *launches);
+// advance (may be null): the restore also opens the next slice, as
+// launch_advance_ctl would (the fused close saves that launch).
 cudaError_t launch_restore(const Params &P, const ScanOut &o, Tuple *scratch, uint32_t cap, asse_superpoint *csip,
-                           asse_superpoint *report, uint64_t out_cap, cudaStream_t s, uint64_t *launches);
+                           asse_superpoint *report, uint64_t out_cap, cudaStream_t s, uint64_t *launches,
+                           SliceCtl *advance = nullptr);
 cudaError_t launch_estimate(const Params &P, uint32_t w, const uint32_t *pool, uint32_t c0, uint32_t kp,
                             const unsigned long long *aat, const uint32_t *aips, uint64_t n, asse_superpoint *out,
                             int sms, cudaStream_t s, uint64_t *launches);

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
     uint32_t *words = sm + (P.g + 1) / 2;                           // [Wd]
     uint32_t *hist_w = words + P.Wd;                                 // [64][32] 16-bit, kept zero between uses
     uint16_t *hist = reinterpret_cast<uint16_t *>(hist_w);
-    uint8_t *act_tab = reinterpret_cast<uint8_t *>(hist_w + HIST_WORDS);  // [g]: ACT of each AT's block
+    RangeDesc *desc = reinterpret_cast<RangeDesc *>(hist_w + HIST_WORDS);  // [Wd]
+    uint32_t *actw = reinterpret_cast<uint32_t *>(desc + P.Wd);             // [Wd]
     __shared__ uint32_t end[65];
     __shared__ uint32_t card;
     __shared__ float pbg;
@@ -118,8 +119,7 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
     for (uint32_t i = tid; i < HIST_WORDS; i += blockDim.x)
         hist_w[i] = 0;
     // the states are packed as of the end of slice k - 1 (block 0's ACT (k-1) mod 2k)
-    for (uint32_t h = tid; h < P.g; h += blockDim.x)
-        act_tab[h] = (uint8_t)act_of(P, (P.k - 1) % P.k2, act_block(P, h));
+    feature_tables<WB>(P, (P.k - 1) % P.k2, P.k, desc, actw);
     __syncthreads();
     for (uint64_t si = blockIdx.x; si < n; si += gridDim.x) {
         const uint64_t key = splitmix(S.seed ^ splitmix(first + si + 0x51ED270B27ull));
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
             uint32_t cnt = 0;
             uint32_t wreg[FEAT_MAXM];
             load_atv_words<WB>(P, words, tid, wreg);
-            atv_features<WB>(P, wreg, act_tab, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
+            atv_features<WB>(P, wreg, desc, actw, P.k, pw, powf(pw, (float)P.r), pw, hist, x + si * FEAT,
                              tid, &cnt);
             if (tid == 0) {
                 log_n[si] = (float)log((double)card);
@@ -619,7 +619,8 @@ int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uin
     const uint32_t Fw = 32 / w;
     P.Wd = ((cfg->g + Fw - 1) / Fw + 7) / 8 * 8;
     SynthArgs S{cfg->seed, cfg->n_max_log2, cfg->bg_max};
-    const size_t smem = ((cfg->g + 1) / 2 + P.Wd + HIST_WORDS) * sizeof(uint32_t) + cfg->g;
+    const size_t smem = ((cfg->g + 1) / 2 + P.Wd + HIST_WORDS) * sizeof(uint32_t) +
+                        (size_t)P.Wd * (sizeof(RangeDesc) + sizeof(uint32_t));
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

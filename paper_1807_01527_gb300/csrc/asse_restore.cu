@@ -66,7 +66,9 @@ __device__ __forceinline__ void emit(Status *st, asse_superpoint *csip, asse_sup
     }
 }
 
-constexpr int RESTORE_THREADS = 256;
+constexpr int RESTORE_THREADS = 512;
+constexpr uint32_t RESTORE_SMEM_TUPLES = 640;  // per level; the rest of a level spills to the global scratch
+constexpr uint32_t RESTORE_SMEM_COLS = 512;    // columns of each row's SA list placed in shared memory
 
 __device__ __forceinline__ void overflow(Status *st, uint32_t needed)
 {
@@ -74,31 +76,52 @@ __device__ __forceinline__ void overflow(Status *st, uint32_t needed)
     atomicMax(&st->needed, (unsigned long long)needed);
 }
 
+// Tuple a of a level: the first RESTORE_SMEM_TUPLES in shared memory, the rest
+// in this frame's part of the global scratch.
+__device__ __forceinline__ Tuple *tuple_at(Tuple *sm, Tuple *gl, uint32_t a)
+{
+    return a < RESTORE_SMEM_TUPLES ? sm + a : gl + a;
+}
+
 __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, ScanOut o, Tuple *scratch, uint32_t cap,
                                                                   asse_superpoint *csip, asse_superpoint *report,
-                                                                  uint64_t out_cap)
+                                                                  uint64_t out_cap, SliceCtl *advance)
 {
+    // the scan of this close has read the slice state; open the next slice
+    if (advance != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+        *advance = slice_ctl(P, advance->t + 1);
     __shared__ uint32_t n_sa[8];
+    __shared__ double p_row[8];  // |AAT(k',i,j)| / (g 2^c) of each row (Sec. 4.3)
     __shared__ uint32_t n_next;
-    __shared__ double up_s;
-    __shared__ int empty;
+    __shared__ Tuple sm_t[2][RESTORE_SMEM_TUPLES];
+    __shared__ uint2 sm_x[4][RESTORE_SMEM_COLS];  // (bits, positions) of the columns of rows 0..3
     const uint32_t j = blockIdx.x;
     const uint32_t cols = P.cmask + 1;
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        empty = 0;
-        for (uint32_t i = 0; i < P.r; i++) {
-            n_sa[i] = o.sa_n[i * P.nf + j];
-            if (n_sa[i] == 0)
-                empty = 1;
-        }
-        up_s = frame_up(P, o.aat, j);
+    // every row's list length and load (one division per thread), and the
+    // columns of rows 0..3 placed on LBS positions, all in one pass
+    if (tid < (int)P.r) {
+        const uint32_t i = tid;
+        n_sa[i] = o.sa_n[i * P.nf + j];
+        p_row[i] = __ddiv_rn((double)o.aat[(size_t)i * P.nf + j], __dmul_rn((double)P.g, (double)(P.cmask + 1)));
     }
+    for (uint32_t e = tid; e < 4 * RESTORE_SMEM_COLS; e += RESTORE_THREADS) {
+        const uint32_t i = e / RESTORE_SMEM_COLS, b = e - i * RESTORE_SMEM_COLS;
+        if (i < P.r && b < o.sa_n[i * P.nf + j]) {
+            uint32_t v, m;
+            place(P, o.sa_x[((size_t)i * P.nf + j) * cols + b], (int)i, v, m);
+            sm_x[i][b] = make_uint2(v, m);
+        }
+    }
+    if (tid == 0)
+        n_next = 0;
     __syncthreads();
-    if (empty)
-        return;
-    Tuple *cur = scratch + (size_t)j * 2 * cap;
-    Tuple *nxt = cur + cap;
+    for (uint32_t i = 0; i < P.r; i++)
+        if (n_sa[i] == 0)
+            return;
+    Tuple *cur_g = scratch + (size_t)j * 2 * cap;
+    Tuple *nxt_g = cur_g + cap;
+    Tuple *cur_s = sm_t[0], *nxt_s = sm_t[1];
     uint32_t n_cur = n_sa[0];
     if (n_cur > cap) {
         if (tid == 0)
@@ -108,32 +131,57 @@ __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, Scan
     // level 0: the columns of SA(0, j)
     for (uint32_t a = tid; a < n_cur; a += RESTORE_THREADS) {
         Tuple t;
-        place(P, o.sa_x[(size_t)j * cols + a], 0, t.L, t.known);
+        if (a < RESTORE_SMEM_COLS) {
+            t.L = sm_x[0][a].x;
+            t.known = sm_x[0][a].y;
+        } else {
+            place(P, o.sa_x[(size_t)j * cols + a], 0, t.L, t.known);
+        }
         t.slot[0] = (uint16_t)a;
-        cur[a] = t;
+        *tuple_at(cur_s, cur_g, a) = t;
     }
-    // levels 1..r-1
+    __syncthreads();
+    // levels 1..r-1: keep a column of row i if it agrees with the tuple on
+    // every position already covered
     for (uint32_t i = 1; i < P.r; i++) {
-        __syncthreads();
-        if (tid == 0)
-            n_next = 0;
-        __syncthreads();
         const uint32_t ni = n_sa[i];
-        const uint64_t total = (uint64_t)n_cur * ni;
         const uint32_t *xs = o.sa_x + ((size_t)i * P.nf + j) * cols;
-        for (uint64_t idx = tid; idx < total; idx += RESTORE_THREADS) {
-            const uint32_t a = (uint32_t)(idx / ni), b = (uint32_t)(idx - (uint64_t)a * ni);
-            const Tuple t = cur[a];
-            uint32_t v, m;
-            place(P, xs[b], (int)i, v, m);
-            if (((t.L ^ v) & m & t.known) == 0) {
-                const uint32_t p = atomicAdd(&n_next, 1u);
-                if (p < cap) {
-                    Tuple t2 = t;
-                    t2.L = t.L | v;
-                    t2.known = t.known | m;
-                    t2.slot[i] = (uint16_t)b;
-                    nxt[p] = t2;
+        // a warp takes one tuple at a time, its lanes the row's columns;
+        // survivors are counted with one shared-memory atomic per warp round
+        const int lane = tid & 31, warp = tid >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        for (uint32_t a = warp; a < n_cur; a += RESTORE_THREADS / 32) {
+            const Tuple t = *tuple_at(cur_s, cur_g, a);
+            for (uint32_t b0 = 0; b0 < ni; b0 += 32) {
+                const uint32_t b = b0 + lane;
+                bool keep = false;
+                uint32_t v = 0, m = 0;
+                if (b < ni) {
+                    if (i < 4 && b < RESTORE_SMEM_COLS) {
+                        const uint2 vm = sm_x[i][b];
+                        v = vm.x;
+                        m = vm.y;
+                    } else {
+                        place(P, xs[b], (int)i, v, m);
+                    }
+                    keep = ((t.L ^ v) & m & t.known) == 0;
+                }
+                const unsigned mk = __ballot_sync(FULL_MASK, keep);
+                if (mk == 0)
+                    continue;
+                uint32_t base = 0;
+                if (lane == 0)
+                    base = atomicAdd(&n_next, (uint32_t)__popc(mk));
+                base = __shfl_sync(FULL_MASK, base, 0);
+                if (keep) {
+                    const uint32_t p = base + __popc(mk & lt);
+                    if (p < cap) {
+                        Tuple t2 = t;
+                        t2.L = t.L | v;
+                        t2.known = t.known | m;
+                        t2.slot[i] = (uint16_t)b;
+                        *tuple_at(nxt_s, nxt_g, p) = t2;
+                    }
                 }
             }
         }
@@ -144,14 +192,20 @@ __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, Scan
                 overflow(o.status, n_cur);
             return;
         }
-        Tuple *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+        Tuple *tmp = cur_s;
+        cur_s = nxt_s;
+        nxt_s = tmp;
+        tmp = cur_g;
+        cur_g = nxt_g;
+        nxt_g = tmp;
+        __syncthreads();  // every thread has read n_next before it is reset
+        if (tid == 0)
+            n_next = 0;
+        __syncthreads();
     }
-    __syncthreads();
     const int lane = tid & 31, warp = tid >> 5;
     for (uint32_t t = warp; t < n_cur; t += RESTORE_THREADS / 32) {
-        const Tuple tu = cur[t];
+        const Tuple tu = *tuple_at(cur_s, cur_g, t);
         uint32_t nat = 0;
         for (uint32_t m = lane; m < P.mw; m += 32) {
             uint32_t acc = FULL_MASK;
@@ -161,11 +215,15 @@ __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, Scan
         }
         nat = __reduce_add_sync(FULL_MASK, nat);
         if (lane == 0) {
+            // UP of the frame: the product over the rows, in row order
+            double up = 1.0;
+            for (uint32_t i = 0; i < P.r; i++)
+                up = __dmul_rn(up, p_row[i]);
             const uint32_t y = (uint32_t)(((uint64_t)tu.L << P.u) | j);
             asse_superpoint sp;
             sp.aip = unmangle(P.Ainv, y);
             sp.nat = nat;
-            eq4(P.g, P.theta, nat, up_s, sp.est, sp.flags);
+            eq4(P.g, P.theta, nat, up, sp.est, sp.flags);
             emit(o.status, csip, report, out_cap, sp);
         }
     }
@@ -210,10 +268,11 @@ __global__ void __launch_bounds__(256) estimate_kernel(Params P, const uint32_t 
 }  // namespace
 
 cudaError_t launch_restore(const Params &P, const ScanOut &o, Tuple *scratch, uint32_t cap, asse_superpoint *csip,
-                           asse_superpoint *report, uint64_t out_cap, cudaStream_t s, uint64_t *launches)
+                           asse_superpoint *report, uint64_t out_cap, cudaStream_t s, uint64_t *launches,
+                           SliceCtl *advance)
 {
     *launches += 1;
-    restore_kernel<<<P.nf, RESTORE_THREADS, 0, s>>>(P, o, scratch, cap, csip, report, out_cap);
+    restore_kernel<<<P.nf, RESTORE_THREADS, 0, s>>>(P, o, scratch, cap, csip, report, out_cap, advance);
     return cudaGetLastError();
 }
 
