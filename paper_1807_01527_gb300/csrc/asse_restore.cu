@@ -43,6 +43,36 @@ __device__ __forceinline__ void eq4(uint32_t g, uint32_t theta, uint32_t nat, do
         flags |= ASSE_SP_REPORTED;
 }
 
+// Eq. 4 for the candidates of one frame, in FP32 where that is provably
+// within 8e-6 relative of the FP64 value above, else by eq4: FP64 on this GPU
+// runs at a small fraction of the FP32 rate, and the restore's FP64 chains
+// were a third of its time.  ln((g-NAT)/(g(1-UP))) = a - b with
+// a = ln(1 - NAT/g) and b = ln(1 - UP).  For NAT < g/2, a = log1pf(-NAT/g):
+// the rounding of NAT/g is amplified at most 1.5x, so a is within 5e-7
+// relative; above, a = logf(g-NAT) - logf(g) of exact integers, within 2e-6
+// absolute (1 ulp of logs below ln 4096) while |a| >= ln 2, so within 3e-6
+// relative.  b = log1pf(-UP) with UP < 1/2 is within 5e-7.  When
+// |a - b| >= max(|a|, |b|) / 2 the difference is within 2 x 3.5e-6, and the
+// product by g and the FP32 result add 1e-7.  The FP64 path takes every
+// ratio near or above 1 and every estimate within 0.1 % of theta, so the
+// report decision is FP64's.
+__device__ __forceinline__ void eq4_fast(uint32_t g, uint32_t theta, uint32_t nat, double up, float b_up,
+                                         float &est, uint32_t &flags)
+{
+    if (nat < g && up < 0.5) {
+        const float a = 2u * nat < g ? log1pf(-(float)nat / (float)g) : logf((float)(g - nat)) - logf((float)g);
+        const float d = a - b_up;
+        const float e = -(float)g * d;
+        if (d < 0.0f && fabsf(d) >= 0.5f * fmaxf(fabsf(a), fabsf(b_up)) &&
+            fabsf(e - (float)theta) > 1e-3f * (float)theta) {
+            est = e;
+            flags = e >= (float)theta ? ASSE_SP_REPORTED : 0u;
+            return;
+        }
+    }
+    eq4(g, theta, nat, up, est, flags);
+}
+
 // UP of a frame (Sec. 4.3): product over rows of |AAT(k',i,j)| / (g 2^c).
 __device__ __forceinline__ double frame_up(const Params &P, const unsigned long long *aat, uint32_t frame)
 {
@@ -223,7 +253,7 @@ __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, Scan
             asse_superpoint sp;
             sp.aip = unmangle(P.Ainv, y);
             sp.nat = nat;
-            eq4(P.g, P.theta, nat, up, sp.est, sp.flags);
+            eq4_fast(P.g, P.theta, nat, up, log1pf(-(float)up), sp.est, sp.flags);
             emit(o.status, csip, report, out_cap, sp);
         }
     }
