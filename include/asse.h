@@ -232,7 +232,10 @@ ASSE_API int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, as
 /* Read the super points reported by the last close/restore: the candidates
  * whose Eq. 4 estimate is >= theta, in unspecified order.  Copies
  * min(count, cap) entries to out (host or device), stores the count in
- * *n_out, and synchronises the stream.  Returns ECAPACITY if cap < count, or
+ * *n_out, and waits for them.  After asse_close_slice, a host read of up to
+ * 4,096 entries waits only for that close (work queued on the stream after
+ * it, such as the next batch's ingest, keeps running); otherwise the call
+ * synchronises the stream.  Returns ECAPACITY if cap < count, or
  * if the restore overflowed restore_cap (then *n_out is the number of
  * column tuples the overflowing join level needed, a lower bound on the
  * capacity to configure, and out is not written).  Errors: ESTATE, ECUDA. */

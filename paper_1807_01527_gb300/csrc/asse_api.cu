@@ -53,6 +53,7 @@ struct asse_pool {
     asse_superpoint *report_host = nullptr;
     uint64_t report_host_cap = 0;
     int report_host_valid = 0;
+    cudaEvent_t close_done = nullptr;  // recorded after those copies: a report waits for its close only
     SliceCtl *ctl = nullptr;  // device copy of the slice-dependent launch arguments
     uint32_t *stage[2] = {nullptr, nullptr};
     uint64_t stage_pairs = 0;
@@ -223,10 +224,15 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
     if (!p->restored)
         return fail(p, ASSE_ESTATE, "no restore since the last scan");
     const bool early = reported && where != ASSE_DEVICE && p->report_host_valid && p->sel == 0;
-    if (!early)
+    if (!early) {
         CK(p, cudaMemcpyAsync(p->status_host, scan_out_w(p, p->sel).status, sizeof(Status), cudaMemcpyDeviceToHost,
                               p->stream));
-    CK(p, cudaStreamSynchronize(p->stream));
+        CK(p, cudaStreamSynchronize(p->stream));
+    } else {
+        // the close and its copies to pinned memory are done; later work
+        // already queued on the stream (the next batch) keeps running
+        CK(p, cudaEventSynchronize(p->close_done));
+    }
     const Status st = *p->status_host;
     if (st.error)
         return fail(p, ASSE_ECUDA, "a bounded device wait of the scan gave up (bulk copy did not complete)");
@@ -282,6 +288,8 @@ void free_all(asse_pool *p)
         cudaFreeHost(p->status_host);
     if (p->report_host)
         cudaFreeHost(p->report_host);
+    if (p->close_done)
+        cudaEventDestroy(p->close_done);
     for (int i = 0; i < 2; i++) {
         if (p->copied[i])
             cudaEventDestroy(p->copied[i]);
@@ -493,6 +501,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     if (e == cudaSuccess)
         e = cudaMallocHost((void **)&p->report_host, p->report_host_cap * sizeof(asse_superpoint));
     if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&p->close_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
         e = cudaEventCreateWithFlags(&p->copied[i], cudaEventDisableTiming);
@@ -665,6 +675,7 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
     CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
     CK(p, cudaMemcpyAsync(p->report_host, p->report, p->report_host_cap * sizeof(asse_superpoint),
                           cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaEventRecord(p->close_done, p->stream));
     p->report_host_valid = 1;
     return ASSE_OK;
 }

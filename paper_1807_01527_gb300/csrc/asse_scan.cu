@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     };
     // tiles are dealt round-robin over all warps of the grid: every tile
     // costs the same, and at any moment the warps stream one contiguous
-    // stretch of the pool (a shared work counter serialises on its atomic)
+    // stretch of the pool
     const uint32_t n_warps = gridDim.x * G.warps;
     uint32_t tile = blockIdx.x * G.warps + warp;
     int b = 0;
