@@ -545,16 +545,22 @@ def main():
     t_ingest = [ev[i][0].elapsed_time(ev[i][1]) / 1e3 for i in range(args.steps)]
     t_close = [ev[i][1].elapsed_time(ev[i][2]) / 1e3 for i in range(args.steps)]
 
-    # end to end through the public API with host buffers: pinned pairs -> H2D
-    # (double-buffered inside asse_ingest) -> ingest -> close -> report on host
+    # end to end through the public API with host buffers: pinned pairs ->
+    # device (asse_ingest returns once the buffer has been read) -> ingest ->
+    # close -> report on the host; as in the device-timed loop, the next
+    # slice's pairs go in before the report of this one is read
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     e2e_pairs, d2h = 0, 0
+    pool.ingest(pinned[args.warmup % n_cycled])
     for i in range(args.steps):
         j = (args.warmup + i) % n_cycled
-        rep = step(j, pinned)
+        pool.close_slice(w.k)
+        if i + 1 < args.steps:
+            pool.ingest(pinned[(args.warmup + i + 1) % n_cycled])
+        rep = pool.report()
         e2e_pairs += n_pairs[j]
         d2h += rep.nbytes + 32
     torch.cuda.synchronize()

@@ -133,12 +133,12 @@ ASSE_API int asse_set_stream(asse_pool *pool, void *stream);
  * pairs: n (aip, bip) uint32 pairs, interleaved (aip0, bip0, aip1, ...).
  *   ASSE_DEVICE: a device address, 16-byte aligned, that must stay valid
  *   until the stream reaches this work; nothing is copied.
- *   ASSE_HOST: host memory.  Pinned (page-locked, device-mapped) memory with a
- *   16-byte aligned device mapping is read in place by the kernel over the
- *   host link; other memory is copied in max_batch chunks into device
- *   staging, the copy of chunk i+1 overlapping the ingest of chunk i.  Either
- *   way the host buffer may be reused when the call returns (the call waits
- *   for the kernel, resp. the last copy).
+ *   ASSE_HOST: host memory (pinned memory gives full copy-engine bandwidth),
+ *   copied in max_batch chunks into device staging, the copy of chunk i+1
+ *   overlapping the ingest of chunk i.  The call returns once the last chunk
+ *   is copied: the host buffer may then be reused, and the ingest of the last
+ *   chunk (and a close queued after it) run on while the caller prepares its
+ *   next batch.
  * Order and repetition of pairs within a slice do not change the result.
  * Errors: EINVAL (NULL with n > 0, misalignment), ECUDA. */
 ASSE_API int asse_ingest(asse_pool *pool, const uint32_t *pairs, uint64_t n, int where);
