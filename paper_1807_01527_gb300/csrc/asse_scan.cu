@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
             }
             unsigned sbits = __ballot_sync(FULL_MASK, sup);
             while (sbits) {
-                // the g-bit active mask of one super ATV, for Algorithm 5
+                // the g-bit active mask of one super ATV, for Algorithm 5;
+                // all 32 lanes share its words (segment by segment in the tile)
                 const uint32_t hl = __ffs(sbits) - 1;
                 sbits &= sbits - 1;
                 const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
@@ -193,11 +194,13 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
                 for (uint32_t k = lane; k < P.mw; k += 32)
                     my_mask[k] = 0;
                 __syncwarp();
-                if (a == a_s) {
+                {
                     constexpr uint32_t F = 32 / WB;
-                    for (uint32_t i = 0; i < G.wseg; i++) {
-                        const uint32_t q = q_first + i;
-                        const uint32_t am = field_bits<WB>(row[i], load_desc(cd_lo, cd_hi, m * n_cd + q + part));
+                    const uint32_t *seg0 = tile_buf[b] + a_s * G.lpa * G.seg_stride;
+                    for (uint32_t q = lane; q < P.Wd; q += 32) {
+                        const uint32_t pq = q / G.wseg;  // the segment holding word q
+                        const uint32_t word = seg0[pq * G.seg_stride + (q - pq * G.wseg)];
+                        const uint32_t am = field_bits<WB>(word, load_desc(cd_lo, cd_hi, m * n_cd + q + pq));
                         if (am) {
                             const uint32_t pos = q * F, off = pos & 31;
                             atomicOr(&my_mask[pos >> 5], am << off);
