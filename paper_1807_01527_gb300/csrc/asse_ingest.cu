@@ -220,10 +220,7 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        static int per_sm[2] = {0, 0};
-        int &occ = per_sm[P.r == 4 ? 0 : 1];
-        if (occ == 0)
-            occ = resident_blocks(kern, INGEST_THREADS, smem);
+        const int occ = resident_blocks(kern, INGEST_THREADS, smem);
         const uint64_t want = (nvec + INGEST_THREADS - 1) / INGEST_THREADS;
         const uint64_t full = (uint64_t)sms * occ;
         // with the count only known on the device, the full resident grid

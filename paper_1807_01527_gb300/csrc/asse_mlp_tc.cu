@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "../../include/asse_learn.h"
@@ -405,15 +406,17 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
 
 EncodeTiled encode_fn()
 {
+    // looked up once per process (the driver's entry point does not change)
+    static std::once_flag once;
     static EncodeTiled fn = nullptr;
-    if (!fn) {
+    std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiled>(p);
-    }
+    });
     return fn;
 }
 
@@ -452,16 +455,12 @@ int launch_mlp_forward_tc(const bf16 *x, uint64_t n, const bf16 *w1p, const bf16
         *why = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
         return 2;
     }
-    static int configured_device = -1;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_device != dev) {
-        if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-            cudaSuccess) {
-            *why = "cannot reserve shared memory for the tensor-core MLP";
-            return 3;
-        }
-        configured_device = dev;
+    if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+        cudaSuccess) {
+        *why = "cannot reserve shared memory for the tensor-core MLP";
+        return 3;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
