@@ -89,19 +89,31 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     const uint32_t cols = P.cmask + 1;
     const uint32_t ntiles = (total_atv + G.apt - 1) / G.apt;
     uint32_t *my_mask = maskbuf + warp * P.mw;
-    uint32_t *tile_buf[2] = {tiles + (2 * warp) * G.tile_words, tiles + (2 * warp + 1) * G.tile_words};
-    uint64_t *bar[2] = {&mbar[2 * warp], &mbar[2 * warp + 1]};
-    uint32_t parity[2] = {0, 0};
+    // buffer b of this warp, its mbarrier and phase parity (bit b of par);
+    // computed, not indexed arrays, so that nothing lives in local memory
+    auto tile_buf = [&](int b) { return tiles + (2 * warp + b) * G.tile_words; };
+    auto bar = [&](int b) { return &mbar[2 * warp + b]; };
+    uint32_t par = 0;
 
+    // Segments of an odd number of 16-byte units need no padding: the tile
+    // is then one contiguous stretch of the pool, fetched with one copy.
+    const bool whole = G.seg_stride == G.wseg;
     auto issue = [&](uint32_t tile, int b) {
         const uint32_t atv0 = tile * G.apt;
         const uint32_t n_atv = min(G.apt, total_atv - atv0);
+        if (whole) {
+            if (lane == 0) {
+                mbar_expect_tx(bar(b), n_atv * P.Wd * 4u);
+                bulk_load(tile_buf(b), pool + (size_t)atv0 * P.Wd, n_atv * P.Wd * 4u, bar(b));
+            }
+            return;
+        }
         if (lane == 0)
-            mbar_expect_tx(bar[b], n_atv * P.Wd * 4u);
+            mbar_expect_tx(bar(b), n_atv * P.Wd * 4u);
         __syncwarp();
         if (a < n_atv)
-            bulk_load(tile_buf[b] + lane * G.seg_stride, pool + (size_t)(atv0 + a) * P.Wd + q_first, G.wseg * 4u,
-                      bar[b]);
+            bulk_load(tile_buf(b) + lane * G.seg_stride, pool + (size_t)(atv0 + a) * P.Wd + q_first, G.wseg * 4u,
+                      bar(b));
     };
     // tiles are dealt round-robin over all warps of the grid: every tile
     // costs the same, and at any moment the warps stream one contiguous
@@ -115,21 +127,21 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     if (next < ntiles)
         issue(next, 1);
     while (tile < ntiles) {
-        if (!__all_sync(FULL_MASK, mbar_wait(bar[b], parity[b]))) {
+        if (!__all_sync(FULL_MASK, mbar_wait(bar(b), (par >> b) & 1u))) {
             // the copy did not land: flag it, give the other copy in flight a
             // bounded chance to finish, and leave
             if (lane == 0)
                 for (uint32_t m = 0; m < nw; m++)
                     atomicExch(&W.o[m].status->error, 1u);
             if (next < ntiles)
-                mbar_wait(bar[b ^ 1], parity[b ^ 1]);
+                mbar_wait(bar(b ^ 1), (par >> (b ^ 1)) & 1u);
             return;
         }
-        parity[b] ^= 1;
+        par ^= 1u << b;
         const uint32_t atv0 = tile * G.apt;
         const uint32_t n_atv = min(G.apt, total_atv - atv0);
         const bool mine = a < n_atv;
-        uint32_t *row = tile_buf[b] + lane * G.seg_stride;
+        uint32_t *row = tile_buf(b) + lane * G.seg_stride;
         uint32_t cnt[NW];
 #pragma unroll
         for (int m = 0; m < NW; m++)
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
                 __syncwarp();
                 {
                     constexpr uint32_t F = 32 / WB;
-                    const uint32_t *seg0 = tile_buf[b] + a_s * G.lpa * G.seg_stride;
+                    const uint32_t *seg0 = tile_buf(b) + a_s * G.lpa * G.seg_stride;
                     for (uint32_t q = lane; q < P.Wd; q += 32) {
                         const uint32_t pq = q / G.wseg;  // the segment holding word q
                         const uint32_t word = seg0[pq * G.seg_stride + (q - pq * G.wseg)];
@@ -237,7 +249,13 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
                 for (uint32_t i = 0; i < G.wseg; i++)
                     row[i] = decay_swar<WB>(row[i]);
                 fence_async_smem();
-                bulk_store(pool + (size_t)atv * P.Wd + q_first, row, G.wseg * 4u);
+                if (!whole)
+                    bulk_store(pool + (size_t)atv * P.Wd + q_first, row, G.wseg * 4u);
+            }
+            if (whole) {
+                __syncwarp();
+                if (lane == 0)
+                    bulk_store(pool + (size_t)atv0 * P.Wd, tile_buf(b), n_atv * P.Wd * 4u);
             }
         }
         // this buffer is free again: fetch the tile after next into it

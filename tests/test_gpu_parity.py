@@ -72,14 +72,16 @@ def test_tiny_saturated_state_and_capacity(mods):
 
 
 # (k, g, r, c, u, s, counter): every counter width 1..8, r from 2 to 8,
-# frames 1..16, g not a multiple of the fields per word
+# frames 1..16, g not a multiple of the fields per word; ATVs of 8 to 88
+# words, so both scan tile layouts (padded lane segments, and whole tiles
+# when a segment is an odd number of 16-byte units) are covered
 CASES = [
     (1, 37, 4, 8, 0, 8, "at"), (2, 29, 4, 8, 0, 8, "at"), (3, 61, 3, 11, 1, 10, "at"),
     (5, 130, 5, 7, 1, 6, "at"), (10, 211, 4, 9, 2, 7, "at"), (20, 97, 8, 6, 2, 4, "at"),
     (40, 257, 4, 8, 0, 8, "at"), (100, 333, 2, 16, 0, 16, "at"),
     (1, 64, 4, 8, 0, 8, "ace"), (3, 50, 4, 9, 2, 7, "ace"), (5, 77, 5, 7, 1, 6, "ace"),
     (10, 128, 4, 8, 0, 8, "ace"), (20, 101, 3, 11, 1, 10, "ace"), (40, 300, 4, 8, 0, 8, "ace"),
-    (100, 250, 4, 8, 0, 8, "ace"),
+    (100, 250, 4, 8, 0, 8, "ace"), (10, 570, 4, 8, 0, 8, "ace"),
 ]
 
 
@@ -226,7 +228,8 @@ def test_link_full_size_three_slices(mods):
 
 @pytest.mark.parametrize("k,g,r,c,u,s,counter,n_win", [
     (6, 150, 4, 9, 2, 7, "at", 3), (10, 211, 4, 9, 2, 7, "at", 4), (5, 77, 5, 7, 1, 6, "ace", 4),
-    (1, 64, 4, 8, 0, 8, "ace", 2), (20, 97, 8, 6, 2, 4, "at", 2)])
+    (1, 64, 4, 8, 0, 8, "ace", 2), (20, 97, 8, 6, 2, 4, "at", 2), (40, 257, 4, 8, 0, 8, "at", 4),
+    (10, 570, 4, 8, 0, 8, "ace", 3)])
 def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
     """One pass over the pool for several windows k' <= k: every window's
     counts, loads, candidates and report equal the oracle's close for that
