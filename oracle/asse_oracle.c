@@ -35,7 +35,8 @@ typedef struct {
     uint32_t A;      /* mangling multiplier, 2 <= A < 2^32 */
     uint64_t bh_a;   /* BH multiplier (odd) */
     uint64_t bh_b;   /* BH offset */
-    uint32_t mode;   /* 0: asynchronous timestamps (Sec. 3); 1: aging counter ACE (Sec. 2.3) */
+    uint32_t mode;   /* 0: asynchronous timestamps (Sec. 3); 1: aging counter ACE (Sec. 2.3);
+                      * 2: asynchronous timestamps with one ACT shared by the whole ATV */
     uint32_t pad;
 } oracle_params;
 
@@ -87,6 +88,11 @@ uint32_t oracle_preserve_at(uint32_t value, uint32_t act, uint32_t k)
  * AT index, so AT h is in block min(h / a, 2k-1). */
 uint32_t oracle_block(const oracle_state *st, uint32_t h)
 {
+    /* Aligned variant (mode 2): the ATV is one block, so every AT has ACT C0
+     * and the whole pool is checked by preserveAT once every k slices
+     * instead of two of 2k blocks every slice. */
+    if (st->p.mode == 2)
+        return 0;
     uint32_t a = st->p.g / (2 * st->p.k);
     uint32_t b = h / a;
     return b < 2 * st->p.k - 1 ? b : 2 * st->p.k - 1;
@@ -193,14 +199,14 @@ static size_t at_index(const oracle_state *st, uint32_t row, uint32_t est, uint3
 
 static uint32_t inactive_value(const oracle_state *st)
 {
-    return st->p.mode == 0 ? 2 * st->p.k : 0;
+    return st->p.mode == 1 ? 0 : 2 * st->p.k;
 }
 
 /* InitAT on every AT of the ATV cube (Sec. 3, Sec. 4). */
 oracle_state *oracle_create(const oracle_params *p)
 {
     if (p->k < 1 || p->k > 127 || p->g < 2 * p->k || p->r < 1 || p->r > 32 || p->c < 1 || p->u > 8 ||
-        p->c + p->u > 24 || p->c > 32 - p->u || p->A < 2 || p->mode > 1)
+        p->c + p->u > 24 || p->c > 32 - p->u || p->A < 2 || p->mode > 2)
         return NULL;
     oracle_state *st = (oracle_state *)calloc(1, sizeof(*st));
     if (!st)
@@ -244,7 +250,7 @@ void oracle_ingest(oracle_state *st, const uint32_t *pairs, uint64_t n)
         uint32_t h = oracle_bh(st, bip);
         for (uint32_t i = 0; i < st->p.r; i++) {
             uint32_t est = (z << st->p.c) | x[i];
-            uint32_t v = st->p.mode == 0 ? oracle_act(st, h) : st->p.k;
+            uint32_t v = st->p.mode == 1 ? st->p.k : oracle_act(st, h);
             st->at[at_index(st, i, est, h)] = (uint8_t)v;
         }
     }

@@ -9,7 +9,9 @@ Sec. 2.3) against facts the paper and plain mathematics fix:
 * the same model for the aging-counter variant;
 * the refresh touches only ATs whose ACT is 0 or k, i.e. two of the 2k blocks
   per slice, once every k slices per block;
-* k = 1 is the discrete window: the pool holds the current slice only.
+* k = 1 is the discrete window: the pool holds the current slice only;
+* the aligned variant (one ACT for the whole ATV) meets the same naive model
+  and checks every AT at once, every k slices.
 """
 import json
 import os
@@ -89,7 +91,8 @@ def _small_params(k, g, seed=3, u=0):
     return p
 
 
-@pytest.mark.parametrize("k,g,mode", [(3, 16, 0), (4, 24, 0), (5, 10, 0), (2, 9, 0), (4, 16, 1), (1, 8, 0)])
+@pytest.mark.parametrize("k,g,mode", [(3, 16, 0), (4, 24, 0), (5, 10, 0), (2, 9, 0), (4, 16, 1), (1, 8, 0),
+                                      (3, 16, 2), (4, 24, 2), (1, 8, 2)])
 def test_whole_pool_matches_naive_timestamps(oracle_mod, k, g, mode):
     """Every AT of a small pool, every slice, every k': the oracle's activity
     equals the naive 'last set at most k'-1 slices ago' model.  The naive
@@ -139,6 +142,30 @@ def test_refresh_touches_two_blocks_per_slice(oracle_mod):
         o.advance()
     for b, ts in seen.items():
         assert np.all(np.diff(ts) == k), (b, ts)
+
+
+def test_aligned_refresh_checks_whole_pool_every_k_slices(oracle_mod):
+    """Aligned variant: every AT shares the ACT C0 = t mod 2k, so preserveAT
+    acts on the whole pool at the slices where C0 is 0 or k and on nothing in
+    between; an AT set at slice t is cleared by the first such check at least
+    k slices later, exactly when the naive model stops counting it."""
+    k, g = 4, 24
+    p = _small_params(k, g)
+    o = oracle_mod.Oracle.from_params(p, mode=2)
+    assert [o.block(h) for h in range(g)] == [0] * g
+    pairs = synth.random_pairs(6, 0, 300, n_hosts=30, n_bips=200)
+    changed_at = []
+    for t in range(5 * k):
+        assert all(o.act(h) == t % (2 * k) for h in range(g))
+        if t % 3 == 0:
+            o.ingest(pairs[(t // 3) * 40:(t // 3) * 40 + 40])
+        before = o.at().copy()
+        o.advance()
+        after = o.at()
+        if not np.array_equal(before, after):
+            changed_at.append(t + 1)
+        assert np.all((after == before) | (after == 2 * k))    # a check only clears
+    assert changed_at and all(t1 % k == 0 for t1 in changed_at), changed_at
 
 
 def test_k1_is_discrete_window(oracle_mod):
