@@ -114,7 +114,7 @@ def oracle_slice_time(w, ingest_sample: int, counter: str = "at"):
     slice, then the whole close (counts, loads, restore, NAT + Eq. 4) and the
     refresh.  Returns (seconds per full slice, extrapolated; sample text)."""
     import oracle
-    o = oracle.Oracle.from_params(w.params, mode=1 if counter == "ace" else 0)
+    o = oracle.Oracle.from_params(w.params, mode={"at": 0, "ace": 1, "aligned": 2}[counter])
     pairs = w.pairs(0)
     sample = pairs[:ingest_sample]
     t0 = time.perf_counter()
@@ -442,8 +442,9 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
     ap.add_argument("--cycled", type=int, default=0,
                     help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
-    ap.add_argument("--counter", default="at", choices=["at", "ace"],
-                    help="at: the paper's asynchronous timestamps; ace: aging counters")
+    ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned"],
+                    help="at: the paper's asynchronous timestamps; ace: aging counters; aligned: timestamps with "
+                         "one ACT per ATV (whole-pool refresh every k slices)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

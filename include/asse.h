@@ -58,6 +58,12 @@ extern "C" {
 /* Counter kinds. */
 #define ASSE_COUNTER_AT 0  /* asynchronous timestamp, log2(2k+1) bits (Sec. 3) */
 #define ASSE_COUNTER_ACE 1 /* aging counter, log2(k+1) bits, decremented every slice (Sec. 2.3) */
+/* Asynchronous timestamps with one ACT for the whole ATV (all 2k blocks of
+ * Sec. 3 aligned): the same counters and Algorithms 1-3, but preserveAT reaches
+ * every AT at once, at the slices where C0 = t mod 2k is 0 or k, instead of two
+ * of 2k blocks every slice.  Results equal the staggered pool's; the refresh
+ * work comes in bursts of the whole pool every k slices. */
+#define ASSE_COUNTER_AT_ALIGNED 2
 
 /* Flags of asse_superpoint. */
 #define ASSE_SP_SATURATED 1u /* NAT == g: Eq. 4 is +infinity */
@@ -78,12 +84,20 @@ extern "C" {
  *  A       mangling multiplier of f(aip) = A*aip mod (2^32+15), 2 <= A < 2^32.
  *  bh_a    BH multiplier (must be odd), bh_b BH offset:
  *          BH(bip) = (hi32(bh_a*bip + bh_b mod 2^64) * g) >> 32.
- *  counter ASSE_COUNTER_AT or ASSE_COUNTER_ACE.
+ *  counter ASSE_COUNTER_AT, ASSE_COUNTER_ACE or ASSE_COUNTER_AT_ALIGNED.
  *  restore_cap  column tuples held per frame at any join level of the
  *          restore; 0 selects 4096.  The candidate lists hold up to
  *          restore_cap * 2^u entries.
  *  max_batch    device staging capacity in pairs for ASSE_HOST ingest
  *          (copied in chunks of this size); 0 selects 4 Mi.
+ *  key_table    ASSE_KEYS_AUTO, ASSE_KEYS_ON or ASSE_KEYS_OFF: whether the
+ *          ingest keeps a device table of the (aip, BH(bip)) keys already set
+ *          in the open slice (4 entries of 8 bytes per ATV, 1 to 32 MiB), so
+ *          that a key repeated across the SMs reaches the pool once.  AUTO
+ *          keeps one when the pool is larger than the device's L2 cache (the
+ *          repeats then cost DRAM sectors); with the pool in L2 a pool word
+ *          costs what a table entry costs.  Results are the same either way.
+ *  pad     must be 0.
  */
 typedef struct asse_config {
     uint32_t k, theta, g, r, c, u, s, A;
@@ -91,7 +105,14 @@ typedef struct asse_config {
     uint32_t counter;
     uint32_t restore_cap;
     uint64_t max_batch;
+    uint32_t key_table;
+    uint32_t pad;
 } asse_config;
+
+/* Values of asse_config.key_table. */
+#define ASSE_KEYS_AUTO 0
+#define ASSE_KEYS_ON 1
+#define ASSE_KEYS_OFF 2
 
 /* One candidate or reported super point (Sec. 4.2-4.3). */
 typedef struct asse_superpoint {
@@ -108,7 +129,7 @@ typedef struct asse_pool_info {
     uint32_t words;      /* 32-bit words per ATV, ceil(g/fields) rounded up to a multiple of 8 */
     uint32_t E;          /* ATVs per row: 2^(c+u); ATV index in a row = (frame << c) | column */
     uint32_t threshold;  /* super-ATV count threshold ceil(g - g*exp(-theta/g)) (Sec. 4.2) */
-    uint32_t block;      /* ATs per ACT block: floor(g/2k) */
+    uint32_t block;      /* ATs per ACT block: floor(g/2k) (g for ASSE_COUNTER_AT_ALIGNED) */
     uint64_t slice;      /* index of the open slice (0 after create) */
     uint64_t pool_words; /* r * E * words */
     const uint32_t *pool;/* device address of the packed pool, [r][E][words] */

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libasse.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE, EAGAIN = 0, 1, 2, 3, 4, 5, 6
 HOST, DEVICE = 0, 1
-COUNTER_AT, COUNTER_ACE = 0, 1
+COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED = 0, 1, 2
+COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED}
+KEY_TABLE = {"auto": 0, "on": 1, "off": 2}
 SP_SATURATED, SP_REPORTED = 1, 2
 
 u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
@@ -26,7 +28,7 @@ u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_voi
 class Config(ctypes.Structure):
     _fields_ = [("k", u32), ("theta", u32), ("g", u32), ("r", u32), ("c", u32), ("u", u32), ("s", u32),
                 ("A", u32), ("bh_a", u64), ("bh_b", u64), ("counter", u32), ("restore_cap", u32),
-                ("max_batch", u64)]
+                ("max_batch", u64), ("key_table", u32), ("pad", u32)]
 
 
 class SuperPoint(ctypes.Structure):
@@ -157,10 +159,11 @@ def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
     return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
 
 
-def make_config(params: dict, counter: str = "at", restore_cap: int = 0, max_batch: int = 0) -> Config:
+def make_config(params: dict, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
+                key_table: str = "auto") -> Config:
     return Config(int(params["k"]), int(params["theta"]), int(params["g"]), int(params["r"]), int(params["c"]),
                   int(params["u"]), int(params["s"]), int(params["A"]), int(params["bh_a"]), int(params["bh_b"]),
-                  COUNTER_ACE if counter == "ace" else COUNTER_AT, int(restore_cap), int(max_batch))
+                  COUNTERS[counter], int(restore_cap), int(max_batch), KEY_TABLE[key_table], 0)
 
 
 class Server:
@@ -248,11 +251,8 @@ class Pool:
     """One ATV cube in device memory (include/asse.h)."""
 
     def __init__(self, params: dict, *, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
-                 stream: int | None = None):
-        cfg = Config(int(params["k"]), int(params["theta"]), int(params["g"]), int(params["r"]), int(params["c"]),
-                     int(params["u"]), int(params["s"]), int(params["A"]), int(params["bh_a"]),
-                     int(params["bh_b"]), COUNTER_ACE if counter == "ace" else COUNTER_AT, int(restore_cap),
-                     int(max_batch))
+                 stream: int | None = None, key_table: str = "auto"):
+        cfg = make_config(params, counter, restore_cap, max_batch, key_table)
         self.cfg = cfg
         self._h = vp()
         self._stream = _current_stream() if stream is None else stream

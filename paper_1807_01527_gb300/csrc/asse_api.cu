@@ -127,8 +127,8 @@ int validate(const asse_config *c, std::string &why)
     auto bad = [&](const char *m) { why = m; return ASSE_EINVAL; };
     if (!c)
         return bad("cfg is NULL");
-    if (c->counter != ASSE_COUNTER_AT && c->counter != ASSE_COUNTER_ACE)
-        return bad("counter must be ASSE_COUNTER_AT or ASSE_COUNTER_ACE");
+    if (c->counter != ASSE_COUNTER_AT && c->counter != ASSE_COUNTER_ACE && c->counter != ASSE_COUNTER_AT_ALIGNED)
+        return bad("counter must be ASSE_COUNTER_AT, ASSE_COUNTER_ACE or ASSE_COUNTER_AT_ALIGNED");
     if (c->k < 1 || c->k > 127)
         return bad("k must be in [1, 127]");
     if (c->g < 2 * c->k || c->g > 4096)
@@ -152,6 +152,8 @@ int validate(const asse_config *c, std::string &why)
         return bad("bh_a must be odd");
     if (c->theta < 1)
         return bad("theta must be >= 1");
+    if (c->key_table > ASSE_KEYS_OFF || c->pad != 0)
+        return bad("key_table must be ASSE_KEYS_AUTO, ASSE_KEYS_ON or ASSE_KEYS_OFF, and pad 0");
     // the scan holds one ATV in a warp tile of at most 512 words
     const uint32_t w = c->counter == ASSE_COUNTER_ACE ? (c->k == 1 ? 1 : ceil_log2(c->k + 1)) : ceil_log2(2 * c->k + 1);
     if ((c->g + 32 / w - 1) / (32 / w) > 512)
@@ -276,6 +278,7 @@ void free_all(asse_pool *p)
     cudaFree(p->report);
     cudaFree(p->status);
     cudaFree(p->ctl);
+    cudaFree(p->P.keys);
     cudaFree(p->stage[0]);
     cudaFree(p->stage[1]);
     cudaFree(p->q_aips);
@@ -372,8 +375,14 @@ uint64_t pool_device_bytes(const asse_config *cfg)
     const uint64_t nf = 1ull << cfg->u, nseg = cfg->r * nf, mw = (cfg->g + 31) / 32;
     const uint64_t cap = cfg->restore_cap ? cfg->restore_cap : 4096;
     const uint64_t stage = cfg->max_batch ? (cfg->max_batch + 1) / 2 * 2 : (4ull << 20);
+    // the key table of asse_create, on the current device
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        cudaGetLastError();
+    const uint32_t klg = key_table_log2(n_atv, n_atv * Wd * 4, (unsigned long long)l2, cfg->key_table);
     return n_atv * Wd * 4 + n_atv * 2 + nseg * (8 + 4) + n_atv * 4 + n_atv * mw * 4 + nf * 2 * cap * sizeof(Tuple) +
-           2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8;
+           2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8 +
+           (klg ? sizeof(unsigned long long) << klg : 0);
 }
 
 int pool_feature_view(asse_pool *p, FeatureView *v)
@@ -436,7 +445,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     p->F = 32 / p->w;
     p->words_used = (cfg->g + p->F - 1) / p->F;
     const uint32_t Wd = (p->words_used + 7) / 8 * 8;
-    p->blk = cfg->g / (2 * k);
+    // the aligned variant is one block of g ATs (every AT has ACT C0)
+    p->blk = cfg->counter == ASSE_COUNTER_AT_ALIGNED ? cfg->g : cfg->g / (2 * k);
     Params &P = p->P;
     P.k = k;
     P.k2 = 2 * k;
@@ -493,6 +503,12 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     alloc((void **)&p->report, p->out_cap * sizeof(asse_superpoint));
     alloc((void **)&p->status, sizeof(Status));
     alloc((void **)&p->ctl, sizeof(SliceCtl));
+    int l2 = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    P.klg = key_table_log2(n_atv, p->pool_words * 4, (unsigned long long)l2, cfg->key_table);
+    if (P.klg)
+        alloc((void **)&P.keys, sizeof(unsigned long long) << P.klg);
     alloc((void **)&p->stage[0], p->stage_pairs * 8);
     alloc((void **)&p->stage[1], p->stage_pairs * 8);
     if (e == cudaSuccess)
@@ -532,6 +548,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream);
+    if (e == cudaSuccess && P.keys)
+        e = cudaMemsetAsync(P.keys, 0xff, sizeof(unsigned long long) << P.klg, p->stream);
     const SliceCtl ctl0 = slice_ctl(P, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, p->stream);
@@ -880,6 +898,9 @@ int asse_load(asse_pool *p, const void *src, uint64_t n)
                           p->stream));
     const SliceCtl c = slice_ctl(p->P, h.slice);
     CK(p, cudaMemcpyAsync(p->ctl, &c, sizeof c, cudaMemcpyHostToDevice, p->stream));
+    // the key table describes the replaced state
+    if (p->P.keys)
+        CK(p, cudaMemsetAsync(p->P.keys, 0xff, sizeof(unsigned long long) << p->P.klg, p->stream));
     CK(p, cudaStreamSynchronize(p->stream));
     p->t = h.slice;
     p->scanned = p->restored = p->refreshed = 0;

@@ -7,13 +7,20 @@
 // key this block already handled in this launch sets exactly the same r
 // fields to the same values, so it is skipped (SetAT is idempotent within a
 // slice; a key pushed out of the table only means a repeat is processed
-// again).  Unseen keys go to a per-warp queue; every 32 queued keys, each
-// lane takes one, computes f(aip), the frame, the r column indices and the
-// ACT of the AT in registers, issues the r word loads together, then sets
-// the r fields; a field that already holds the slice's value costs one load
-// and no atomic.  The table is 64 KB: the rest of the SM's 256 KB of L1 /
-// shared memory stays L1 cache, which serves the pool words of keys the
-// table missed (a 128 KB table ran 13 % slower, a 192 KB one 2x slower).
+// again).  Unseen keys go to a per-warp queue.  A pool larger than the L2
+// cache also has a key table in device memory shared by every block and
+// every ingest of the slice: every 32 queued keys, each lane claims one there
+// (one L2 access), and only keys new to the slice go on, through a second
+// per-warp queue, to Algorithm 3: each lane takes one, computes f(aip), the
+// frame, the r column indices and the ACT of the AT in registers, issues the
+// r word loads together, then sets the r fields; a field that already holds
+// the slice's value costs one load and no atomic.  Across the 152 blocks a
+// hot key reaches the pool once instead of once per block, which spares r
+// DRAM sectors per repeat; with the pool in L2 a pool word costs what a claim
+// costs, so such pools have no key table.  The shared-memory table is 64 KB:
+// the rest of the SM's 256 KB of L1 / shared memory stays L1 cache, which
+// serves the pool words of keys the table missed (a 128 KB table ran 13 %
+// slower, a 192 KB one 2x slower).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,20 +30,6 @@
 namespace asse {
 
 namespace {
-
-template <int WB>
-__device__ __forceinline__ void prep_pair(const Params &P, uint32_t c0, uint32_t aip, uint32_t bip, uint64_t &LL,
-                                          uint32_t &z, uint32_t &q, uint32_t &sh, uint32_t &val)
-{
-    constexpr uint32_t F = 32 / WB;
-    const uint32_t f = mangle(P.A, aip);
-    z = f & (P.nf - 1);
-    LL = lbs_twice(P, f);
-    const uint32_t h = bip_hash(P, bip);
-    q = h / F;
-    sh = (h - q * F) * WB;
-    val = P.ace ? P.k : act_of(P, c0, act_block(P, h));
-}
 
 // SetAT on one packed field; old is a possibly stale read of the word.
 // Within a slice every writer of a field writes the same value, so the bits
@@ -75,7 +68,8 @@ constexpr int INGEST_THREADS = 1024;
 constexpr int INGEST_WARPS = INGEST_THREADS / 32;
 constexpr int INGEST_BLOCKS_PER_SM = 1;
 constexpr uint32_t SEEN_LOG2 = 13;  // 8,192 keys = 64 KB of shared memory per block
-constexpr uint32_t QCAP = 96;       // per-warp queue of new keys (below 32 between rounds, + 64)
+constexpr uint32_t QCAP = 96;       // per-warp queue of keys new to the block (below 32 between rounds, + 64)
+constexpr uint32_t Q2CAP = 64;      // per-warp queue of keys new to the slice (below 32 between rounds, + 32)
 constexpr unsigned long long NO_KEY = ~0ull;  // BH values are < 2^16, so never a real key
 
 __device__ __forceinline__ uint32_t seen_slot(uint32_t aip, uint32_t h)
@@ -92,6 +86,40 @@ __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t a
         return true;
     seen[s] = key;
     return false;
+}
+
+// A bijection of the 48-bit value aip * 2^16 + h (h < 4096): two odd
+// multiplications modulo 2^48, each followed by an xor-shift.  Its top klg
+// bits pick the key table slot and the other 48 - klg bits are the tag, so
+// (slot, tag) identifies the key exactly.
+__device__ __forceinline__ unsigned long long key_mix(uint32_t aip, uint32_t h)
+{
+    constexpr unsigned long long M48 = (1ull << 48) - 1;
+    unsigned long long x = ((unsigned long long)aip << 16) | h;
+    x = (x * 0x9E3779B97F4Bull) & M48;
+    x ^= x >> 23;
+    x = (x * 0xC2B2AE3D27D5ull) & M48;
+    x ^= x >> 21;
+    return x;
+}
+
+// True if this lane is the first of the slice to claim key (aip, h) in the
+// key table shared by all blocks.  A key that another block (or an earlier
+// ingest of the same slice) claimed has had, or will have by the end of this
+// launch, its r fields set to the same values, so it is skipped.  A key
+// pushed out of the table by another only costs a repeat.  The plain read
+// first spares the exchange for the keys already claimed, most of them.
+__device__ __forceinline__ bool claim_key(const Params &P, uint32_t gen, uint32_t aip, uint32_t h, bool ok)
+{
+    if (!ok)
+        return false;
+    const unsigned long long x = key_mix(aip, h);
+    const uint32_t tb = 48 - P.klg;
+    const unsigned long long want = ((unsigned long long)gen << 32) | (x & ((1ull << tb) - 1));
+    unsigned long long *slot = P.keys + (x >> tb);
+    if (__ldcg(slot) == want)
+        return false;
+    return atomicExch(slot, want) != want;
 }
 
 // Algorithm 3 for one key (aip, h = BH(bip)) of this lane, if ok: f(aip), the
@@ -128,32 +156,58 @@ __device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_
             set_field(a[i], o[i], sh, val, FM);
 }
 
+// Keys new to the block (one per lane, if ok) are claimed in the key table;
+// the ones new to the slice join the warp's second queue, and every 32 of
+// those run Algorithm 3 with all lanes busy.  Without a key table, Algorithm
+// 3 runs on them directly.
+template <int WB, int R>
+__device__ __forceinline__ void claim_and_set(const Params &P, uint32_t *pool, uint32_t c0, uint32_t gen, int r,
+                                              uint2 e, bool ok, uint2 *q2, uint32_t &q2n, unsigned lt)
+{
+    bool run = ok;
+    if (P.keys != nullptr) {
+        const bool fresh = claim_key(P, gen, e.x, e.y, ok);
+        const unsigned m = __ballot_sync(FULL_MASK, fresh);
+        if (fresh)
+            q2[q2n + __popc(m & lt)] = e;
+        q2n += __popc(m);
+        run = q2n >= 32;
+        if (run) {
+            __syncwarp();
+            q2n -= 32;
+            e = q2[q2n + threadIdx.x % 32];
+            __syncwarp();
+        }
+    }
+    set_key<WB, R>(P, pool, c0, r, e.x, e.y, run);
+}
+
 template <int WB, int R>
 __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     ingest_kernel(Params P, uint32_t *pool, const uint32_t *__restrict__ pairs_raw, uint64_t n_arg,
                   const unsigned long long *n_dev, const SliceCtl *ctl)
 {
     const uint32_t c0 = ctl->c0;
+    const uint32_t gen = (uint32_t)ctl->t;
     const uint64_t n = n_dev ? *n_dev : n_arg;
     const uint64_t nvec = n / 2;
     const uint4 *__restrict__ pairs = reinterpret_cast<const uint4 *>(pairs_raw);
     const uint2 *__restrict__ tail = (n & 1) ? reinterpret_cast<const uint2 *>(pairs_raw + 2 * (n - 1)) : nullptr;
-    constexpr uint32_t FM = (1u << WB) - 1;
     extern __shared__ unsigned long long seen[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint2 *queue = reinterpret_cast<uint2 *>(seen + (1u << SEEN_LOG2)) + warp * QCAP;
+    uint2 *queue = reinterpret_cast<uint2 *>(seen + (1u << SEEN_LOG2)) + warp * (QCAP + Q2CAP);
+    uint2 *q2 = queue + QCAP;
     for (uint32_t i = threadIdx.x; i < (1u << SEEN_LOG2); i += blockDim.x)
         seen[i] = NO_KEY;
     __syncthreads();
     const int r = R ? R : (int)P.r;
     // Warp-uniform loop: the 32 lanes of a warp take 32 consecutive vectors.
-    // Keys the table has not seen go to the warp's queue; whenever it holds
-    // 32 of them, every lane runs Algorithm 3 on one, so the long path runs
-    // with all lanes busy however many repeats the table removed.
+    // Keys the block's table has not seen go to the warp's queue; whenever it
+    // holds 32 of them, every lane claims one in the slice's key table.
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t base0 = (uint64_t)blockIdx.x * blockDim.x + warp * 32u;
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t qn = 0;
+    uint32_t qn = 0, q2n = 0;
     // the next round's pairs are loaded before this round's are processed,
     // so the stream's DRAM latency overlaps the pool accesses
     uint4 pr = base0 + lane < nvec ? __ldcs(pairs + base0 + lane) : make_uint4(0, 0, 0, 0);
@@ -182,24 +236,23 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
             qn -= 32;
             const uint2 e = queue[qn + lane];
             __syncwarp();
-            set_key<WB, R>(P, pool, c0, r, e.x, e.y, true);
+            claim_and_set<WB, R>(P, pool, c0, gen, r, e, true, q2, q2n, lt);
         }
     }
     __syncwarp();
     if (qn > 0) {
         const bool ok = lane < qn;
-        const uint2 e = ok ? queue[lane] : make_uint2(0, 0);
-        set_key<WB, R>(P, pool, c0, r, e.x, e.y, ok);
+        claim_and_set<WB, R>(P, pool, c0, gen, r, ok ? queue[lane] : make_uint2(0, 0), ok, q2, q2n, lt);
+    }
+    __syncwarp();
+    if (q2n > 0) {
+        const bool ok = lane < q2n;
+        const uint2 f = ok ? q2[lane] : make_uint2(0, 0);
+        set_key<WB, R>(P, pool, c0, r, f.x, f.y, ok);
     }
     if (tail != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
         const uint2 pr1 = *tail;
-        uint64_t LL;
-        uint32_t z, q, sh, val;
-        prep_pair<WB>(P, c0, pr1.x, pr1.y, LL, z, q, sh, val);
-        for (int i = 0; i < r; i++) {
-            uint32_t *a = field_word(P, pool, i, z, LL, q);
-            set_field(a, *a, sh, val, FM);
-        }
+        set_key<WB, R>(P, pool, c0, r, pr1.x, bip_hash(P, pr1.y), true);
     }
 }
 
@@ -213,7 +266,8 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
         return cudaSuccess;
     const uint64_t nvec = n / 2;
     *launches += 1;
-    const size_t smem = (sizeof(unsigned long long) << SEEN_LOG2) + (size_t)INGEST_WARPS * QCAP * sizeof(uint2);
+    const size_t smem =
+        (sizeof(unsigned long long) << SEEN_LOG2) + (size_t)INGEST_WARPS * (QCAP + Q2CAP) * sizeof(uint2);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         auto kern = P.r == 4 ? ingest_kernel<WB, 4> : ingest_kernel<WB, 0>;
@@ -234,7 +288,7 @@ namespace {
 
 __global__ void advance_ctl_kernel(Params P, SliceCtl *ctl)
 {
-    *ctl = slice_ctl(P, ctl->t + 1);
+    open_next_slice(P, ctl);
 }
 
 __global__ void reset_kernel(unsigned long long *aat, uint32_t *sa_n, uint32_t nseg, Status *status)
@@ -252,7 +306,7 @@ __global__ void reset_kernel(unsigned long long *aat, uint32_t *sa_n, uint32_t n
 cudaError_t launch_advance_ctl(const Params &P, SliceCtl *ctl, cudaStream_t s, uint64_t *launches)
 {
     *launches += 1;
-    advance_ctl_kernel<<<1, 1, 0, s>>>(P, ctl);
+    advance_ctl_kernel<<<1, 256, 0, s>>>(P, ctl);
     return cudaGetLastError();
 }
 

@@ -28,7 +28,28 @@ struct Params {
     uint64_t Ainv;      // A^-1 mod p (may exceed 2^32)
     uint64_t bh_a, bh_b;
     uint32_t xshift[8]; // 2W - c - s*i: shift of the doubled LBS giving x_i
+    // Table of the (aip, BH(bip)) keys set in the open slice, shared by every
+    // ingest block: 2^klg 64-bit entries, each a tag of the key and the low
+    // 32 bits of the slice (all ones = empty).  Null for a pool that fits in
+    // the L2 cache.
+    unsigned long long *keys;
+    uint32_t klg;
 };
+
+// Key table size for a pool of n_atv ATVs: 4 entries per ATV, 2^17 .. 2^22,
+// or none (0): with ASSE_KEYS_OFF, or with ASSE_KEYS_AUTO when the pool's
+// bytes fit in an L2 cache of l2_bytes.  (At least 2^17 entries keeps a tag
+// below 2^31, so no entry is all ones.)
+inline uint32_t key_table_log2(unsigned long long n_atv, unsigned long long pool_bytes,
+                               unsigned long long l2_bytes, uint32_t mode)
+{
+    if (mode == ASSE_KEYS_OFF || (mode == ASSE_KEYS_AUTO && pool_bytes <= l2_bytes))
+        return 0;
+    uint32_t lg = 17;
+    while (lg < 22 && (1ull << lg) < 4 * n_atv)
+        lg++;
+    return lg;
+}
 
 // Device-resident status of one close, reset by every scan.
 struct Status {
@@ -79,21 +100,32 @@ struct SliceCtl {
     Refresh R;
 };
 
-// Words holding the two ACT blocks whose ACT becomes 0 and k when slice
-// t_new opens (blocks are contiguous: the first 2k-1 of blk ATs, the last the
-// rest of g).
+// Words holding the ACT blocks whose ACT becomes 0 or k when slice t_new
+// opens.  Blocks are contiguous: the first 2k-1 of blk ATs, the last the rest
+// of g.  blk == g is the aligned variant: the ATV is one block with ACT C0,
+// which reaches 0 or k once every k slices (no range in between).
 __host__ __device__ inline Refresh refresh_for(uint32_t k, uint32_t g, uint32_t blk, uint32_t F,
                                                unsigned long long t_new)
 {
     const uint32_t k2 = 2 * k;
+    const uint32_t nblk = blk >= g ? 1 : k2;
     Refresh R{};
     R.c0n = (uint32_t)(t_new % k2);
     const uint32_t b[2] = {(k2 - R.c0n) % k2, (k + k2 - R.c0n) % k2};
-    uint32_t lo[2], hi[2];
+    uint32_t lo[2] = {0, 0}, hi[2] = {0, 0}, n = 0;
     for (int i = 0; i < 2; i++) {
-        const uint32_t flo = b[i] * blk, fhi = b[i] == k2 - 1 ? g : (b[i] + 1) * blk;
-        lo[i] = flo / F;
-        hi[i] = (fhi - 1) / F;
+        if (b[i] >= nblk)
+            continue;
+        const uint32_t flo = b[i] * blk, fhi = b[i] == nblk - 1 ? g : (b[i] + 1) * blk;
+        lo[n] = flo / F;
+        hi[n] = (fhi - 1) / F;
+        n++;
+    }
+    if (n < 2) {
+        R.q_lo[0] = lo[0];
+        R.q_hi[0] = hi[0];
+        R.n_ranges = n;
+        return R;
     }
     if (lo[1] < lo[0]) {
         const uint32_t a = lo[0], c = hi[0];
@@ -124,6 +156,23 @@ __host__ __device__ inline SliceCtl slice_ctl(const Params &P, unsigned long lon
     c.R = refresh_for(P.k, P.g, P.blk, P.F, t + 1);
     return c;
 }
+
+#ifdef __CUDACC__
+// Open the slice after ctl->t; every thread of one block calls this.  The
+// ingest's key table tags its entries with the low 32 bits of the slice, so
+// when those wrap to 0 the block empties the table: entries of the previous
+// 2^32 slices would otherwise match again.
+__device__ inline void open_next_slice(const Params &P, SliceCtl *ctl)
+{
+    const unsigned long long tn = ctl->t + 1;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        *ctl = slice_ctl(P, tn);
+    if ((uint32_t)tn == 0 && P.keys != nullptr)
+        for (uint32_t i = threadIdx.x; i < (1u << P.klg); i += blockDim.x)
+            P.keys[i] = ~0ull;
+}
+#endif
 
 struct ScanOut {
     uint16_t *cnt;

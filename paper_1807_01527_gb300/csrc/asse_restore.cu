@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(RESTORE_THREADS) restore_kernel(Params P, Scan
                                                                   uint64_t out_cap, SliceCtl *advance)
 {
     // the scan of this close has read the slice state; open the next slice
-    if (advance != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
-        *advance = slice_ctl(P, advance->t + 1);
+    if (advance != nullptr && blockIdx.x == 0)
+        open_next_slice(P, advance);
     __shared__ uint32_t n_sa[8];
     __shared__ double p_row[8];  // |AAT(k',i,j)| / (g 2^c) of each row (Sec. 4.3)
     __shared__ uint32_t n_next;

@@ -82,6 +82,9 @@ CASES = [
     (1, 64, 4, 8, 0, 8, "ace"), (3, 50, 4, 9, 2, 7, "ace"), (5, 77, 5, 7, 1, 6, "ace"),
     (10, 128, 4, 8, 0, 8, "ace"), (20, 101, 3, 11, 1, 10, "ace"), (40, 300, 4, 8, 0, 8, "ace"),
     (100, 250, 4, 8, 0, 8, "ace"), (10, 570, 4, 8, 0, 8, "ace"),
+    # one ACT for the whole ATV: the refresh reaches every word every k slices
+    (1, 37, 4, 8, 0, 8, "aligned"), (4, 130, 4, 9, 2, 7, "aligned"), (10, 512, 4, 8, 0, 8, "aligned"),
+    (12, 1024, 4, 8, 0, 8, "aligned"),
 ]
 
 
@@ -90,8 +93,9 @@ def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
     asse, oracle, torch = mods
     theta = max(4, g // 3)
     p = _params(k, g, r, c, u, s, theta, seed=k + g)
-    mode = 1 if counter == "ace" else 0
-    pool = asse.Pool(p, counter=counter, restore_cap=1 << 14)
+    mode = {"at": 0, "ace": 1, "aligned": 2}[counter]
+    # half of the cases with the ingest's key table (small pools have none by default)
+    pool = asse.Pool(p, counter=counter, restore_cap=1 << 14, key_table="on" if (k + g) % 2 else "auto")
     orc = oracle.Oracle.from_params(p, mode=mode)
     heavy = [theta // 2, theta, 2 * theta, 3 * theta]
     n_slices = min(2 * k + 3, 40) if k > 10 else 2 * k + 3
@@ -107,6 +111,37 @@ def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
         orc.advance()
         np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
     pool.close()
+
+
+def test_aligned_stepwise_and_staggered_equivalence(mods):
+    """The aligned pool through the stepwise calls (scan, restore, the
+    separate refresh kernel of asse_advance) equals the oracle's aligned mode,
+    and its per-ATV counts equal the staggered pool's on the same input: both
+    count exactly the ATs set in the latest k' slices."""
+    asse, oracle, torch = mods
+    p = _params(5, 200, 4, 9, 2, 7, 60, seed=8)
+    al = asse.Pool(p, counter="aligned")
+    st = asse.Pool(p)
+    orc = oracle.Oracle.from_params(p, mode=2)
+    assert al.info()["block"] == 200
+    for t in range(24):
+        pairs = mixed_pairs(8, t, 3001, [40, 90, 300])
+        for pl in (al, st):
+            pl.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        kp = 1 + t % 5
+        al.scan(kp)
+        st.close_slice(kp)
+        cnt = orc.counts(kp)
+        np.testing.assert_array_equal(al.counts(), cnt)
+        np.testing.assert_array_equal(st.counts(), cnt, err_msg=f"staggered t={t}")
+        al.restore()
+        compare_lists(al.candidates(), orc.close_report(kp)["candidates"], p["theta"], "csip")
+        al.advance()
+        orc.advance()
+        np.testing.assert_array_equal(al.state(), orc.at(), err_msg=f"after refresh t={t}")
+    for pl in (al, st):
+        pl.close()
 
 
 def test_stepwise_equals_fused_and_estimate(mods):
@@ -176,6 +211,57 @@ def test_host_ingest_chunks_and_snapshot(mods):
     with pytest.raises(asse.AsseError) as ei:
         bad.load(img)
     assert ei.value.status == asse.EINVAL
+
+
+def test_key_table_repeats_and_slice_wrap(mods):
+    """The ingest skips a (aip, BH(bip)) key already set in the open slice,
+    remembered in a key table shared by all blocks and tagged with the low 32
+    bits of the slice.  Batches that repeat and overlap within a slice, with a
+    stepwise scan in between, give the oracle's state; a pool loaded at slice
+    2^32 - 1 (the same ACT phase, k = 4) passes the tag wrap, where the table
+    is emptied, and stays equal to the pool it was copied from."""
+    import ctypes
+    asse, oracle, torch = mods
+    p = _params(4, 128, 4, 10, 0, 8, 64, seed=5)
+    a = asse.Pool(p, key_table="on")
+    orc = oracle.Oracle.from_params(p)
+    s0 = ((1 << 32) - 1) % 8          # slices 2^32 - 1 and s0 share C0 = t mod 2k
+    for t in range(s0):
+        x = mixed_pairs(5, t, 6001, [150, 300])
+        y = np.concatenate([x[::3], mixed_pairs(5, 100 + t, 2001, [150])])
+        for batch in (x, x, y):
+            a.ingest(to_device(batch))
+            orc.ingest(batch)
+        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after repeated batches t={t}")
+        a.scan(4)
+        a.ingest(to_device(x[::2]))
+        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after a batch past a scan t={t}")
+        check_close(a, orc, 4)
+        orc.advance()
+        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after refresh t={t}")
+    img = bytearray(a.snapshot())
+    off = 16 + ctypes.sizeof(asse.Config)
+    assert int.from_bytes(img[off:off + 8], "little") == s0
+    img[off:off + 8] = ((1 << 32) - 1).to_bytes(8, "little")
+    b = asse.Pool(p, key_table="on")
+    b.load(bytes(img))
+    assert b.info()["slice"] == (1 << 32) - 1
+    for t in range(s0, s0 + 4):
+        x = mixed_pairs(5, t, 7001, [200, 300])
+        for pl in (a, b):
+            pl.ingest(to_device(x))
+            pl.ingest(to_device(x[::2]))
+        orc.ingest(x)
+        np.testing.assert_array_equal(b.read_pool(), a.read_pool(), err_msg=f"slice {t}")
+        np.testing.assert_array_equal(a.state(), orc.at())
+        check_close(a, orc, 4)
+        b.close_slice(4)
+        orc.advance()
+        np.testing.assert_array_equal(b.read_pool(), a.read_pool(), err_msg=f"after close {t}")
+        assert sorted(b.report()["aip"].tolist()) == sorted(a.report()["aip"].tolist())
+    assert b.info()["slice"] == (1 << 32) + 3
+    for pl in (a, b):
+        pl.close()
 
 
 def test_edge_cases(mods):
