@@ -442,6 +442,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
     ap.add_argument("--cycled", type=int, default=0,
                     help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
+    ap.add_argument("--clocks-dir", default="", help="where the nvidia-smi clock samples of the timed region go "
+                                                      "(default: the temporary directory)")
     ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned"],
                     help="at: the paper's asynchronous timestamps; ace: aging counters; aligned: timestamps with "
                          "one ACT per ATV (whole-pool refresh every k slices)")
@@ -472,9 +474,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    clocks = Clocks(os.path.join(out_dir if os.path.isdir(out_dir) else tempfile.gettempdir(),
-                                 "bench_clocks_%d.csv" % rank), local)
+    clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), "bench_clocks_%d.csv" % rank), local)
 
     dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
     pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host]

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     const uint2 *__restrict__ tail = (n & 1) ? reinterpret_cast<const uint2 *>(pairs_raw + 2 * (n - 1)) : nullptr;
     extern __shared__ unsigned long long seen[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint2 *queue = reinterpret_cast<uint2 *>(seen + (1u << SEEN_LOG2)) + warp * (QCAP + Q2CAP);
+    // the second queue only exists with a key table (its 16 KB otherwise stay L1 cache)
+    uint2 *queue = reinterpret_cast<uint2 *>(seen + (1u << SEEN_LOG2)) + warp * (QCAP + (P.keys ? Q2CAP : 0));
     uint2 *q2 = queue + QCAP;
     for (uint32_t i = threadIdx.x; i < (1u << SEEN_LOG2); i += blockDim.x)
         seen[i] = NO_KEY;
@@ -266,8 +267,8 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
         return cudaSuccess;
     const uint64_t nvec = n / 2;
     *launches += 1;
-    const size_t smem =
-        (sizeof(unsigned long long) << SEEN_LOG2) + (size_t)INGEST_WARPS * (QCAP + Q2CAP) * sizeof(uint2);
+    const size_t smem = (sizeof(unsigned long long) << SEEN_LOG2) +
+                        (size_t)INGEST_WARPS * (QCAP + (P.keys ? Q2CAP : 0)) * sizeof(uint2);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
         auto kern = P.r == 4 ? ingest_kernel<WB, 4> : ingest_kernel<WB, 0>;
