@@ -34,10 +34,12 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # learned estimator: 68 used features -> 256 -> 256 -> 1 (multiply-adds x 2)
 MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
-# dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch on the link
-# workload, from the ncu capture summarised in profiles/ingest_link.md (caches
-# flushed by ncu); None for other workloads or until the current kernel is captured
-INGEST_TRAFFIC_LINK = 203_198_208
+# dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch, from the ncu
+# captures summarised in profiles/ingest_link.md and profiles/ingest_long.md
+# (caches flushed by ncu; the long workload's capture is of its slice 0, 33.5 M
+# pairs); None for the other workloads and counters
+INGEST_TRAFFIC = {("link", "at"): (202_891_264, "ncu capture, profiles/ingest_link.md"),
+                  ("long", "at"): (1_321_334_528, "ncu capture of the slice-0 launch, profiles/ingest_long.md")}
 
 
 def workload_desc(w) -> dict:
@@ -602,8 +604,9 @@ def main():
             "host_call_ms_p50": {k: 1e3 * statistics.median(v) for k, v in host_t.items()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": INGEST_TRAFFIC_LINK if (args.workload, args.counter) == ("link", "at") else None,
-                         "traffic_source": "ncu capture, profiles/ingest_link.md", "kernel": "ingest",
+                         "traffic": INGEST_TRAFFIC.get((args.workload, args.counter), (None, None))[0],
+                         "traffic_source": INGEST_TRAFFIC.get((args.workload, args.counter), (None, None))[1],
+                         "kernel": "ingest",
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
                          "model": "8 B per pair + 32 B x r per distinct (aip, bip) pair",
                          "distinct_pair_fraction": statistics.mean(n_distinct[j] / n_pairs[j] for j in used)},
