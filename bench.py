@@ -179,6 +179,26 @@ def make_slices(w, n_slices: int):
     return [r[0] for r in res], [r[1] for r in res]
 
 
+def random_sector_rate(pool, stream, n_reads: int = 1 << 26, runs: int = 3) -> dict:
+    """Random-access roofline: the rate of independent random 4-byte reads
+    (one 32-byte sector each) of the pool's own words, CUDA events on the
+    pool's stream, median of `runs` after one warm-up."""
+    import torch
+    pool.probe_random_reads(n_reads)
+    ts = []
+    for _ in range(runs):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        issued = pool.probe_random_reads(n_reads)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    t = statistics.median(ts)
+    l2 = getattr(torch.cuda.get_device_properties(torch.cuda.current_device()), "L2_cache_size", 0)
+    return {"gbs": issued * 32 / t / 1e9, "reads_per_s": issued / t, "pool_bytes": 4 * pool.info()["pool_words"],
+            "l2_bytes": int(l2)}
+
+
 def reduce_over_ranks(times, counts, device):
     """Whole-job figures of the replicas: the slowest rank's times (max) and
     the units all ranks processed (sum)."""
@@ -570,6 +590,7 @@ def main():
     e2e_elapsed = time.perf_counter() - t0
     clk = clocks.stop(wall0, wall1)
     breakdown = stepwise_breakdown(pool, dev, w, args.warmup) if args.breakdown else None
+    sector = random_sector_rate(pool, stream)
 
     if world > 1:
         elapsed, e2e_elapsed, pairs_done, e2e_pairs = reduce_over_ranks([elapsed, e2e_elapsed],
@@ -610,6 +631,12 @@ def main():
                          "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
                          "model": "8 B per pair + 32 B x r per distinct (aip, bip) pair",
                          "distinct_pair_fraction": statistics.mean(n_distinct[j] / n_pairs[j] for j in used)},
+            "random_sector_roofline": {
+                "peak": sector["gbs"], "unit": "GB/s", "frac": achieved / sector["gbs"],
+                "reads_per_s": sector["reads_per_s"],
+                "what": "random 4-byte reads of this pool's words (one 32-byte sector each, every SM busy), "
+                        "timed in this run (pool of %d MB, L2 of %d MB); the ingest's algorithmic bytes per launch "
+                        "over its time, against this rate" % (sector["pool_bytes"] >> 20, sector["l2_bytes"] >> 20)},
             "e2e": {"value": e2e_pairs / e2e_elapsed, "unit": "pkts/s",
                     "h2d_bytes_per_step": int(8 * n_avg), "d2h_bytes_per_step": int(d2h / args.steps)},
             "gpu_launches": int(launches),

@@ -291,6 +291,17 @@ ASSE_API int asse_snapshot(asse_pool *pool, void *dst, uint64_t cap, uint64_t *n
  * same cfg (checked).  Synchronises.  Errors: EINVAL (mismatch), ECUDA. */
 ASSE_API int asse_load(asse_pool *pool, const void *src, uint64_t n);
 
+/* Measurement aid, no counterpart in the paper: enqueue on the pool's stream
+ * at least n_reads (<= 2^34) independent random 4-byte reads of the pool's
+ * own packed words (one 32-byte sector each, spread over every SM), and
+ * store the number actually issued in *n_issued (may be NULL).  The pool is
+ * not changed.  Timed by the caller with events around the call, this gives
+ * the random-sector read rate of a buffer of the pool's size, in L2 or in
+ * HBM as the pool is: the random-access roofline of the ingest, whose pool
+ * traffic is r random words per pair new to the slice.  Does not
+ * synchronise.  Errors: EINVAL, ECUDA. */
+ASSE_API int asse_probe_random_reads(asse_pool *pool, uint64_t n_reads, uint64_t *n_issued);
+
 /* Number of kernels this pool has launched since creation. */
 ASSE_API uint64_t asse_launches(const asse_pool *pool);
 

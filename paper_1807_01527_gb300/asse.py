@@ -71,6 +71,7 @@ EXPORTS = {
     "asse_read_pool": (i32, [vp, vp, i32]),
     "asse_snapshot": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
     "asse_load": (i32, [vp, vp, u64]),
+    "asse_probe_random_reads": (i32, [vp, u64, ctypes.POINTER(u64)]),
     "asse_launches": (u64, [vp]),
     "asse_last_error": (ctypes.c_char_p, [vp]),
     "asse_strerror": (ctypes.c_char_p, [i32]),
@@ -380,6 +381,13 @@ class Pool:
         buf = ctypes.create_string_buffer(n.value)
         self._check(lib().asse_snapshot(self._h, buf, n.value, ctypes.byref(n)))
         return buf.raw
+
+    def probe_random_reads(self, n_reads: int) -> int:
+        """Enqueue >= n_reads random 4-byte reads of the pool's words on its
+        stream (a measurement aid); returns the number issued."""
+        n = u64(0)
+        self._check(lib().asse_probe_random_reads(self._h, int(n_reads), ctypes.byref(n)))
+        return int(n.value)
 
     def load(self, image: bytes):
         self._check(lib().asse_load(self._h, image, len(image)))

@@ -876,6 +876,20 @@ int asse_snapshot(asse_pool *p, void *dst, uint64_t cap, uint64_t *n_out)
     return ASSE_OK;
 }
 
+int asse_probe_random_reads(asse_pool *p, uint64_t n_reads, uint64_t *n_issued)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    if (n_reads > (1ull << 34))
+        return fail(p, ASSE_EINVAL, "n_reads must be at most 2^34");
+    uint64_t issued = 0;
+    if (n_reads > 0)
+        CK(p, launch_random_reads(p->pool, p->pool_words, n_reads, p->sms, p->stream, &p->launches, &issued));
+    if (n_issued)
+        *n_issued = issued;
+    return ASSE_OK;
+}
+
 int asse_load(asse_pool *p, const void *src, uint64_t n)
 {
     if (!p || !src)

@@ -214,6 +214,11 @@ cudaError_t launch_estimate(const Params &P, uint32_t w, const uint32_t *pool, u
                             const unsigned long long *aat, const uint32_t *aips, uint64_t n, asse_superpoint *out,
                             int sms, cudaStream_t s, uint64_t *launches);
 
+// At least n_reads random 4-byte reads of buf[0, n_words) on stream s, with
+// every SM busy (asse_probe.cu); *issued receives the number launched.
+cudaError_t launch_random_reads(const uint32_t *buf, uint64_t n_words, uint64_t n_reads, int sms, cudaStream_t s,
+                                uint64_t *launches, uint64_t *issued);
+
 // What asse_restore_static (asse_static.cu) needs from a pool: the launch
 // constants, the last scan's outputs and the stream.  Returns ASSE_ESTATE if
 // the pool has no scan to restore from.

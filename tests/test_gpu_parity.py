@@ -264,6 +264,24 @@ def test_key_table_repeats_and_slice_wrap(mods):
         pl.close()
 
 
+def test_random_read_probe_leaves_pool_unchanged(mods):
+    """The random-read probe (the ingest's random-access roofline) issues at
+    least the reads asked for, on the pool's stream, and changes nothing."""
+    asse, oracle, torch = mods
+    w = synth.workload("tiny_b")
+    pool = asse.Pool(w.params)
+    pool.ingest(to_device(w.pairs(0)))
+    before = pool.read_pool()
+    assert pool.probe_random_reads(0) == 0
+    n = pool.probe_random_reads(1 << 20)
+    assert n >= 1 << 20
+    np.testing.assert_array_equal(pool.read_pool(), before)
+    with pytest.raises(asse.AsseError) as ei:
+        pool.probe_random_reads((1 << 34) + 1)
+    assert ei.value.status == asse.EINVAL
+    pool.close()
+
+
 def test_edge_cases(mods):
     asse, oracle, torch = mods
     p = _params(3, 40, 4, 8, 0, 8, 10, seed=9)
