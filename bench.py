@@ -464,6 +464,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
     ap.add_argument("--cycled", type=int, default=0,
                     help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
+    ap.add_argument("--key-table", default="auto", choices=["auto", "on", "off"],
+                    help="the ingest's slice-wide key table (auto: for pools larger than L2)")
     ap.add_argument("--clocks-dir", default="", help="where the nvidia-smi clock samples of the timed region go "
                                                       "(default: the temporary directory)")
     ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned"],
@@ -506,7 +508,7 @@ def main():
     # 8-byte read of every pair plus one 32-byte sector for each of the r AT
     # words of every distinct pair (n_distinct, counted above)
     stream = torch.cuda.current_stream()
-    pool = asse.Pool(w.params, counter=args.counter, stream=stream.cuda_stream)
+    pool = asse.Pool(w.params, counter=args.counter, stream=stream.cuda_stream, key_table=args.key_table)
 
     def step(i, src):
         pool.ingest(src[i % n_cycled])
@@ -610,7 +612,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(workload_desc(w), counter=args.counter.upper(),
+            "config": dict(workload_desc(w), counter=args.counter.upper(), key_table=args.key_table,
                            parallelism="replicas" if world > 1 else "single",
                            l2="inputs cycle over %d distinct slices (%d MB) held in HBM, more than L2; the pool "
                               "state stays resident across steps" % (n_cycled, sum(p.nbytes for p in host) >> 20)),
