@@ -88,21 +88,6 @@ __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t a
     return false;
 }
 
-// A bijection of the 48-bit value aip * 2^16 + h (h < 4096): two odd
-// multiplications modulo 2^48, each followed by an xor-shift.  Its top klg
-// bits pick the key table slot and the other 48 - klg bits are the tag, so
-// (slot, tag) identifies the key exactly.
-__device__ __forceinline__ unsigned long long key_mix(uint32_t aip, uint32_t h)
-{
-    constexpr unsigned long long M48 = (1ull << 48) - 1;
-    unsigned long long x = ((unsigned long long)aip << 16) | h;
-    x = (x * 0x9E3779B97F4Bull) & M48;
-    x ^= x >> 23;
-    x = (x * 0xC2B2AE3D27D5ull) & M48;
-    x ^= x >> 21;
-    return x;
-}
-
 // True if this lane is the first of the slice to claim key (aip, h) in the
 // key table shared by all blocks.  A key that another block (or an earlier
 // ingest of the same slice) claimed has had, or will have by the end of this

@@ -51,6 +51,21 @@ inline uint32_t key_table_log2(unsigned long long n_atv, unsigned long long pool
     return lg;
 }
 
+// A bijection of the 48-bit value aip * 2^16 + h (h < 4096): two odd
+// multiplications modulo 2^48, each followed by an xor-shift.  Its top klg
+// bits pick the ingest's key table slot and the other 48 - klg bits are the
+// tag, so (slot, tag) identifies the key exactly.
+__host__ __device__ __forceinline__ unsigned long long key_mix(uint32_t aip, uint32_t h)
+{
+    constexpr unsigned long long M48 = (1ull << 48) - 1;
+    unsigned long long x = ((unsigned long long)aip << 16) | h;
+    x = (x * 0x9E3779B97F4Bull) & M48;
+    x ^= x >> 23;
+    x = (x * 0xC2B2AE3D27D5ull) & M48;
+    x ^= x >> 21;
+    return x;
+}
+
 // Device-resident status of one close, reset by every scan.
 struct Status {
     unsigned long long n_csip;    // candidates restored (Algorithm 4)
