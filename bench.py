@@ -34,12 +34,35 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # learned estimator: 68 used features -> 256 -> 256 -> 1 (multiply-adds x 2)
 MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
-# dram__bytes_read.sum + dram__bytes_write.sum of one ingest launch, from the ncu
-# captures summarised in profiles/ingest_link.md and profiles/ingest_long.md
-# (caches flushed by ncu; the long workload's capture is of its slice 0, 33.5 M
-# pairs); None for the other workloads and counters
-INGEST_TRAFFIC = {("link", "at"): (202_891_264, "ncu capture, profiles/ingest_link.md"),
-                  ("long", "at"): (1_321_334_528, "ncu capture of the slice-0 launch, profiles/ingest_long.md")}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
+# capture of the kernel, keyed by (workload, counter, kernel): the bytes and
+# the id of the kernel source they were taken from (kernel_source_id below).
+# A figure whose source id no longer matches the current sources is reported
+# as null (the kernel has changed since the capture).
+TRAFFIC = {}
+KERNEL_SOURCES = {
+    "ingest": ["asse_ingest.cu", "asse_device.cuh", "asse_internal.h"],
+    "scan": ["asse_scan.cu", "asse_swar.cuh", "asse_bytes.h", "asse_device.cuh", "asse_internal.h", "asse_ptx.cuh"],
+}
+
+
+def kernel_source_id(kernel: str) -> str:
+    """First 12 hex digits of the SHA-256 of the kernel's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1807_01527_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_of(workload: str, counter: str, kernel: str):
+    """(bytes per launch or None, capture id or None, whether it is current)."""
+    t = TRAFFIC.get((workload, counter, kernel))
+    if t is None:
+        return None, None, False
+    current = t[1] == kernel_source_id(kernel)
+    return (t[0] if current else None), t[1], current
 
 
 def workload_desc(w) -> dict:
@@ -111,47 +134,48 @@ class Clocks:
                 "reasons": sorted({n for r in inside for n in r[3]}), "samples": len(inside), "where": where}
 
 
-def oracle_slice_time(w, ingest_sample: int, counter: str = "at"):
-    """The CPU oracle as it stands (single thread): ingest a sample of one
-    slice, then the whole close (counts, loads, restore, NAT + Eq. 4) and the
-    refresh.  Returns (seconds per full slice, extrapolated; sample text)."""
+def oracle_slice_time(w, pairs, counter: str = "at", orc=None):
+    """The CPU oracle on every host core (its multi-threaded calls: the pool
+    split by row and frame range): ingest one whole slice, then the close
+    (counts, loads, restore, NAT + Eq. 4) and the refresh.  Returns (seconds,
+    cores, description, the oracle)."""
     import oracle
-    o = oracle.Oracle.from_params(w.params, mode={"at": 0, "ace": 1, "aligned": 2}[counter])
-    pairs = w.pairs(0)
-    sample = pairs[:ingest_sample]
+    if orc is None:
+        orc = oracle.Oracle.from_params(w.params, mode={"at": 0, "ace": 1, "aligned": 2}[counter])
+    cores = oracle.cores()
     t0 = time.perf_counter()
-    o.ingest(sample)
-    t_ing = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    o.close_report(w.k, cap=1 << 20)
-    o.advance()
-    t_close = time.perf_counter() - t0
-    per_slice = t_ing * (len(pairs) / len(sample)) + t_close
-    text = ("oracle (1 thread): ingest of the first %d pairs of slice 0 timed and scaled to the %d pairs of a "
-            "slice, plus one full close (counts, loads, restore, NAT, Eq. 4) and refresh of the %s pool (%s counters)"
-            % (len(sample), len(pairs), w.name, counter.upper()))
-    return per_slice, text, len(pairs)
+    orc.ingest(pairs, threads=cores)
+    orc.close_report(w.k, cap=1 << 16, threads=cores)
+    orc.advance(threads=cores)
+    dt = time.perf_counter() - t0
+    text = ("oracle on %d host threads: ingest of one whole slice (%d pairs), its close (counts, loads, restore, "
+            "NAT, Eq. 4) and refresh, %s workload, %s counters" % (cores, pairs.shape[0], w.name, counter.upper()))
+    return dt, cores, text, orc
 
 
 def run_reference(args, w):
-    """--impl reference: the oracle timed on the host, each step one bounded
-    sample of the workload (see oracle_slice_time)."""
+    """--impl reference: the oracle on every host core, each step one whole
+    slice of the workload (the slices cycled as in the GPU leg)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
-    text, n = "", w.n_per_slice
+    n_cycled = min(2, args.cycled or 2)
+    host, _ = make_slices(w, n_cycled)
+    times, pairs_done = [], 0
+    text, cores, orc = "", 1, None
     for i in range(args.warmup + args.steps):
-        per_slice, text, n = oracle_slice_time(w, args.ref_sample, args.counter)
+        p = host[i % n_cycled]
+        dt, cores, text, orc = oracle_slice_time(w, p, args.counter, orc)
         if i >= args.warmup:
-            times.append(per_slice)
-    ms = 1e3 * statistics.mean(times)
-    value = n / (ms / 1e3)
+            times.append(dt)
+            pairs_done += p.shape[0]
+    total = sum(times)
+    value = pairs_done / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pkts/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_desc(w),
-            "cpu_baseline": {"value": value, "unit": "pkts/s", "cores": 1, "kind": "oracle", "sample": text},
+            "cpu_baseline": {"value": value, "unit": "pkts/s", "cores": cores, "kind": "oracle", "sample": text},
             "e2e": {"value": value, "unit": "pkts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -270,36 +294,63 @@ def gen_batch_gpu(n: int, seed: int, n_hosts: int = 1 << 20, alpha: float = 1.1)
     return torch.where(out >= (1 << 31), out - (1 << 32), out).to(torch.int32).contiguous()
 
 
-def learned_accuracy(asse, w, stream, torch):
-    """Train the model on synthetic states shaped like w's ATVs (GPU generator
-    and training kernels), then the mean relative error on held-out states
-    against Eq. 2's."""
+def learned_accuracy(asse, w, stream, torch, loss_kind: str = "rel_mse", n_train: int = 1_800_000,
+                     n_test: int = 200_000, n_max_log2: int = 20, bg_max: float = 0.08, epochs: int = 3):
+    """Train the model on synthetic states shaped like w's ATVs (the GPU
+    generator and training kernels): n_train states with cardinality
+    log-uniform in [1, 2^n_max_log2] spread over the window, background up to
+    bg_max per AT and slice; then the mean relative error on n_test held-out
+    states, over the whole range and by range of the true cardinality, for
+    the model alone, for the learned estimate with its Eq. 2 fallback, and
+    for Eq. 2 alone."""
     keys = synth.method_keys(1)
-    n_max_log2 = 14
-    scfg = dict(k=w.k, g=w.g, r=w.r, n_max_log2=n_max_log2, bg_max=0.01, seed=11, bh_a=keys["bh_a"],
+    scfg = dict(k=w.k, g=w.g, r=w.r, n_max_log2=n_max_log2, bg_max=bg_max, seed=11, bh_a=keys["bh_a"],
                 bh_b=keys["bh_b"])
-    xs, lns, _lcs = asse.synth_states(scfg, 0, 200_000, stream=stream.cuda_stream)
-    xt, lnt, lct = asse.synth_states(scfg, 10_000_000, 20_000, stream=stream.cuda_stream)
+    xs, lns, _lcs = asse.synth_states(scfg, 0, n_train, stream=stream.cuda_stream)
+    xt, lnt, lct = asse.synth_states(scfg, 1 << 40, n_test, stream=stream.cuda_stream)
     trained = asse.MLP(seed=2, stream=stream.cuda_stream)
+    trained.set_loss(loss_kind)
     gen = torch.Generator(device="cuda").manual_seed(0)
-    perm = torch.randperm(xs.shape[0], device="cuda", generator=gen)
-    bs, n_train = 4096, 600
+    bs = 4096
+    n_steps = epochs * (n_train // bs)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for step in range(n_train):
-        o = (step * bs) % xs.shape[0]
+    perm = None
+    for step in range(n_steps):
+        o = (step * bs) % (n_train - n_train % bs)
+        if o == 0:
+            perm = torch.randperm(n_train, device="cuda", generator=gen)
         idx = perm[o:o + bs]
-        trained.train_step(xs[idx].contiguous(), lns[idx].contiguous(), 2e-3 if step < 400 else 5e-4)
+        lr = 2e-3 if step < 0.6 * n_steps else (5e-4 if step < 0.85 * n_steps else 1e-4)
+        trained.train_step(xs[idx].contiguous(), lns[idx].contiguous(), lr)
     t1.record(stream)
     yt = trained.forward(xt)
     trained.check()
-    n_true = torch.exp(lnt)
-    return {"states": "k=%d, g=%d, cardinalities log-uniform in [1, 2^%d], background <= 1%% per AT and slice"
-                      % (w.k, w.g, n_max_log2),
-            "train_rows": n_train * bs, "train_ms": t0.elapsed_time(t1),
-            "mre_mlp": torch.mean(torch.abs(torch.exp(yt) - n_true) / n_true).item(),
-            "mre_eq2": torch.mean(torch.abs(lct - n_true) / n_true).item(), "held_out": int(xt.shape[0])}
+    n_true = torch.exp(lnt.double())
+    lnmax = n_max_log2 * float(np.log(2.0))
+    cnt = xt[:, 0].double() * w.g
+    # the rule of asse_estimate_learned: the model unless the ATV is empty or
+    # the model is above its training range; then Eq. 2
+    inside = (cnt > 0.5) & (yt <= lnmax)
+    est_mlp = torch.exp(yt.double())
+    est_rule = torch.where(inside, torch.exp(torch.clamp(yt.double(), min=0.0)), lct.double())
+    rel = {name: (torch.abs(e - n_true) / n_true) for name, e in
+           (("mlp", est_mlp), ("learned_with_fallback", est_rule), ("eq2", lct.double()))}
+    bins = {}
+    edges = [0, 4, 8, 12, 16, n_max_log2 + 1]
+    lg = lnt.double() / np.log(2.0)
+    for a, b in zip(edges[:-1], edges[1:]):
+        sel = (lg >= a) & (lg < b)
+        if int(sel.sum()) == 0:
+            continue
+        bins["2^%d..2^%d" % (a, min(b, n_max_log2))] = {k: v[sel].mean().item() for k, v in rel.items()}
+    return {"states": "k=%d, g=%d, r=%d, cardinalities log-uniform in [1, 2^%d] spread over the window with random "
+                      "shares, background up to %.2f per AT and slice; %d training and %d held-out states"
+                      % (w.k, w.g, w.r, n_max_log2, bg_max, n_train, n_test),
+            "loss": loss_kind, "train_rows": n_steps * bs, "train_ms": t0.elapsed_time(t1),
+            "mre": {k: v.mean().item() for k, v in rel.items()}, "mre_by_range": bins,
+            "fallback_fraction": 1.0 - inside.double().mean().item()}
 
 
 def run_learned(args):
@@ -340,7 +391,10 @@ def run_learned(args):
     t_mlp = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)) / 1e3
     peak, src_peak = peaks("bf16_tflops")
     achieved = rows * MLP_FLOP_PER_ROW / t_mlp / 1e12
-    acc = None if args.no_accuracy else learned_accuracy(asse, w, stream, torch)
+    # accuracy on the learned-estimator workload: link-shaped states (k=10, g=512)
+    wl = synth.workload("link", seed=1)
+    acc = None if args.no_accuracy else {kind: learned_accuracy(asse, wl, stream, torch, kind)
+                                         for kind in ("rel_mse", "log_mse")}
     line = {"metric": "learned per-ATV inference: feature rows + MLP per scanned slice", "value": rows / (t_feat + t_mlp),
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "mode": "learned",
             "ms_per_step": 1e3 * (t_feat + t_mlp), "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
@@ -447,81 +501,185 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="link", choices=["tiny_b", "link", "long"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-sample", type=int, default=1 << 20)
-    ap.add_argument("--breakdown", action="store_true", help="also time scan / restore / refresh separately")
-    ap.add_argument("--mode", default="slice", choices=["slice", "serve", "learned"],
-                    help="slice: one pool, the headline line; serve: the multi-stream serving loop; "
-                         "learned: per-slice learned inference (features + tensor-core MLP)")
-    ap.add_argument("--serve-slices", type=int, default=12)
-    ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
-    ap.add_argument("--cycled", type=int, default=0,
-                    help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
-    ap.add_argument("--key-table", default="auto", choices=["auto", "on", "off"],
-                    help="the ingest's slice-wide key table (auto: for pools larger than L2)")
-    ap.add_argument("--clocks-dir", default="", help="where the nvidia-smi clock samples of the timed region go "
-                                                      "(default: the temporary directory)")
-    ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned"],
-                    help="at: the paper's asynchronous timestamps; ace: aging counters; aligned: timestamps with "
-                         "one ACT per ATV (whole-pool refresh every k slices)")
-    args = ap.parse_args()
-    args.warmup = max(3, args.warmup)
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.mode in ("serve", "learned"):
-        if rank == 0:
-            (run_serve if args.mode == "serve" else run_learned)(args)
-        return
-    w = synth.workload(args.workload, seed=1 + rank)
-    if args.impl == "reference":
-        run_reference(args, w)
-        return
+def _slice_and_keys(job):
+    """Slice t of a workload and its distinct (aip, bip) keys (a spawned
+    worker of the accuracy leg)."""
+    from oracle import truth
+    name, seed, t = job
+    p = synth.workload(name, seed=seed).pairs(t)
+    return p, truth.slice_keys(p)
 
-    # inputs: distinct slices cycled through, resident in HBM (more than L2:
-    # 512 MB for the link workload, about 1 GB for the long one) and the same
-    # slices in pinned host memory
-    n_cycled = args.cycled or (N_SLICES_CYCLED if w.n_per_slice <= (8 << 20) else 4)
-    host, n_distinct = make_slices(w, n_cycled)
+
+def _rates_summary(rows: list) -> dict:
+    """Mean FPR / FNR / FTR over the windows that hold super points."""
+    rows = [r for r in rows if r["fpr"] is not None]
+    if not rows:
+        return {"windows": 0}
+    return {"windows": len(rows), "fpr": statistics.mean(r["fpr"] for r in rows),
+            "fnr": statistics.mean(r["fnr"] for r in rows), "ftr": statistics.mean(r["ftr"] for r in rows),
+            "super_points_mean": statistics.mean(r["n"] for r in rows)}
+
+
+def run_accuracy(args):
+    """Detection accuracy on the workload's ground truth (exact window
+    cardinalities, Sec. 2.1), as FPR / FNR / FTR (Sec. 5), of:
+      - the sliding pool with Eq. 4 (the paper's method), every slice;
+      - the same candidates judged by the learned candidate model instead of
+        Eq. 4 (trained here on synthetic candidate states shaped like the
+        pool: k, g, r and the row loads the first window shows);
+      - the discrete-window mode (1-bit aging counters, k = 1, reset after
+        every window of k slices) at equal memory: the same words per ATV,
+        so 32 x words ATs of one bit each, judged at the end of each window."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    w = synth.workload(args.workload, seed=1)
+    k = w.k
+    T = args.acc_slices or (3 * k if w.n_per_slice <= (8 << 20) else k + 3)
+    ex = cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn"))
+    futs = [ex.submit(_slice_and_keys, (w.name, w.seed, t)) for t in range(T)]
 
     import torch
+    from oracle import truth
     from paper_1807_01527_gb300 import asse, build
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), "bench_clocks_%d.csv" % rank), local)
-
-    dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
-    pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host]
-    n_pairs = [p.shape[0] for p in host]
-    # Algorithm 3 sets r ATs per pair; repeating an identical (aip, bip) pair
-    # within a slice changes nothing, so the work a slice requires is the
-    # 8-byte read of every pair plus one 32-byte sector for each of the r AT
-    # words of every distinct pair (n_distinct, counted above)
     stream = torch.cuda.current_stream()
+    sliding = asse.Pool(w.params, stream=stream.cuda_stream, restore_cap=1 << 14)
+    words = sliding.info()["words"]
+    p1 = dict(w.params, k=1, g=32 * words)
+    discrete = asse.Pool(p1, counter="ace", stream=stream.cuda_stream, restore_cap=1 << 14)
+    mem = {"sliding_bytes": 4 * sliding.info()["pool_words"], "discrete_bytes": 4 * discrete.info()["pool_words"],
+           "sliding": "g=%d ATs of %d bits" % (w.g, sliding.info()["w"]),
+           "discrete": "g=%d ATs of 1 bit (k=1 aging counters, reset every %d slices)" % (p1["g"], k)}
+    keys, model, model_info = [], None, None
+    max_log_n = 20 * float(np.log(2.0))
+    res = {"eq4": [], "learned": [], "discrete": []}
+    t0 = time.time()
+    for t in range(T):
+        pairs, kt = futs[t].result()
+        keys.append(kt)
+        dev = torch.from_numpy(pairs.view(np.int32)).cuda()
+        sliding.ingest(dev)
+        discrete.ingest(dev)
+        del pairs
+        sliding.scan(k)
+        if model is None and t == k - 1:
+            # row loads of the first full window -> background of the training states
+            P = sliding.loads().astype(np.float64) / (w.g * (1 << w.c))
+            p_slice = 1.0 - (1.0 - float(P.max())) ** (1.0 / k)
+            model, model_info = train_candidate_model(asse, w, stream, torch, bg_max=min(1.0, 2.0 * p_slice),
+                                                      n_max_log2=20)
+        sliding.restore()
+        cand = sliding.candidates()
+        if t >= k - 1:
+            true_sp = truth.super_points(keys[t - k + 1:t + 1], w.theta)
+            res["eq4"].append(truth.error_rates({int(a) for a in cand["aip"][cand["est"] >= w.theta]}, true_sp))
+            learned = set()
+            if cand.size:
+                y = model.forward(sliding.candidate_features(cand["aip"])).cpu().numpy().astype(np.float64)
+                est = np.where(y <= max_log_n, np.exp(np.maximum(y, 0.0)), cand["est"].astype(np.float64))
+                learned = {int(a) for a in cand["aip"][est >= w.theta]}
+            res["learned"].append(truth.error_rates(learned, true_sp))
+        sliding.advance()
+        if (t + 1) % k == 0:
+            discrete.close_slice(1)
+            rep = discrete.report()
+            res["discrete"].append(truth.error_rates({int(a) for a in rep["aip"]},
+                                                     truth.super_points(keys[t - k + 1:t + 1], w.theta)))
+        if t >= k:
+            keys[t - k] = None
+    ex.shutdown()
+    line = {"metric": "detection accuracy on exact window cardinalities: FPR, FNR, FTR (Sec. 5)", "mode": "accuracy",
+            "config": dict(workload_desc(w), slices=T), "data": "synthetic",
+            "sliding_eq4": _rates_summary(res["eq4"]), "sliding_learned_candidates": _rates_summary(res["learned"]),
+            "discrete_1bit_equal_memory": _rates_summary(res["discrete"]), "memory": mem,
+            "candidate_model": model_info, "wall_s": time.time() - t0,
+            "per_window": {kk: [(r["n"], r["n_plus"], r["n_minus"]) for r in v] for kk, v in res.items()}}
+    print(json.dumps(line), flush=True)
+
+
+def train_candidate_model(asse, w, stream, torch, bg_max: float, n_max_log2: int = 20, n_train: int = 1_200_000,
+                          n_test: int = 100_000, epochs: int = 3):
+    """The learned replacement of Eq. 4: an MLP trained with the relative
+    loss on synthetic candidate states of w's shape (k, g, r), background up
+    to bg_max per AT and slice in each row.  Returns (model, summary with the
+    held-out mean relative error of the model and of Eq. 4)."""
+    keys = synth.method_keys(w.seed)
+    cfg = dict(k=w.k, g=w.g, r=w.r, n_max_log2=n_max_log2, bg_max=bg_max, seed=41, bh_a=keys["bh_a"],
+               bh_b=keys["bh_b"])
+    x, ln, _e4 = asse.synth_candidates(cfg, 0, n_train, stream=stream.cuda_stream)
+    xt, lnt, e4t = asse.synth_candidates(cfg, 1 << 40, n_test, stream=stream.cuda_stream)
+    m = asse.MLP(seed=6, stream=stream.cuda_stream)
+    m.set_loss("rel_mse")
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    bs = 4096
+    n_steps = epochs * (n_train // bs)
+    perm = None
+    for step in range(n_steps):
+        o = (step * bs) % (n_train - n_train % bs)
+        if o == 0:
+            perm = torch.randperm(n_train, device="cuda", generator=gen)
+        idx = perm[o:o + bs]
+        lr = 2e-3 if step < 0.6 * n_steps else (5e-4 if step < 0.85 * n_steps else 1e-4)
+        m.train_step(x[idx].contiguous(), ln[idx].contiguous(), lr)
+    y = m.forward(xt)
+    m.check()
+    n_true = torch.exp(lnt.double())
+    e4 = torch.where(torch.isinf(e4t), torch.full_like(e4t, 1e12), e4t).double()
+    rel_m = torch.abs(torch.exp(y.double()) - n_true) / n_true
+    rel_e = torch.abs(e4 - n_true) / n_true
+    near = (lnt >= np.log(w.theta / 4.0)) & (lnt < np.log(4.0 * w.theta))
+    return m, {"states": "k=%d, g=%d, r=%d, cardinalities log-uniform in [1, 2^%d], per-row background up to %.4f "
+                         "per AT and slice; %d training, %d held-out" % (w.k, w.g, w.r, n_max_log2, bg_max, n_train,
+                                                                         n_test),
+               "mre_model": rel_m.mean().item(), "mre_eq4": rel_e.mean().item(),
+               "mre_model_near_theta": rel_m[near].mean().item(), "mre_eq4_near_theta": rel_e[near].mean().item()}
+
+
+def scan_alg_bytes(w, pool_info: dict, counter: str) -> float:
+    """Algorithmic bytes of one fused scan: the pool read once, plus the words
+    the refresh rewrites: the two ACT blocks whose ACT becomes 0 or k (2 of
+    the 2k blocks of every ATV, Algorithm 2) for timestamps, every word
+    every k slices for the aligned variant (averaged per slice), every word
+    for aging counters."""
+    pool_bytes = 4.0 * pool_info["pool_words"]
+    if counter == "ace":
+        return 2 * pool_bytes
+    if counter == "aligned":
+        return pool_bytes * (1.0 + 1.0 / w.k)
+    return pool_bytes * (1.0 + 2.0 / (2 * w.k))
+
+
+def roofline_entry(kernel: str, alg_bytes: float, t_s: float, peak: float, peak_src: str, model: str,
+                   workload: str, counter: str) -> dict:
+    traffic, capture, current = traffic_of(workload, counter, kernel)
+    achieved = alg_bytes / t_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_capture": capture if current else None,
+            "kernel": kernel, "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
+            "ms_per_launch": 1e3 * t_s, "model": model}
+
+
+def bench_workload(w, args, world, rank, stream, torch, asse, dist, with_e2e=True):
+    """One workload: ingest + fused close per step, device-timed over
+    args.steps steps with inputs resident in HBM, then end to end from pinned
+    host buffers.  Returns the measurements (rank-local times and counts)."""
+    n_cycled = args.cycled or (N_SLICES_CYCLED if w.n_per_slice <= (8 << 20) else 4)
+    host, n_distinct = args.slices_of(w, n_cycled)
+    dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
+    pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host] if with_e2e else None
+    n_pairs = [p.shape[0] for p in host]
     pool = asse.Pool(w.params, counter=args.counter, stream=stream.cuda_stream, key_table=args.key_table)
 
-    def step(i, src):
-        pool.ingest(src[i % n_cycled])
-        pool.close_slice(w.k)
-        return pool.report()
-
     for i in range(args.warmup):
-        step(i, dev)
+        pool.ingest(dev[i % n_cycled])
+        pool.close_slice(w.k)
+        pool.report()
     torch.cuda.synchronize()
 
     # device-timed region: inputs resident, per-kernel events on the pool stream
+    pool.set_timing(True)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    lat = []
+    lat, t_scan, t_restore = [], [], []
     launches0 = pool.launches
     if world > 1:
         dist.barrier()
@@ -530,13 +688,13 @@ def main():
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    pairs_done = 0
-    n_reported = 0
+    pairs_done, n_reported = 0, 0
     # Step i: ingest slice i, close it, read its report on the host.  The
     # next slice's ingest is queued before the report is read (the report
     # waits for its own close only), so the device does not idle while the
     # host reads.
     host_t = {"ingest_call": [], "close_call": [], "report_call": []}
+
     def src_of(i):
         return dev[(args.warmup + i) % n_cycled]
     ev[0][0].record(stream)
@@ -554,6 +712,9 @@ def main():
         h1 = time.perf_counter()
         rep = pool.report()
         t2 = time.perf_counter()
+        sc, rs = pool.close_timing()
+        t_scan.append(sc / 1e3)
+        t_restore.append(rs / 1e3)
         lat.append(t2 - t0)
         host_t["close_call"].append(t1 - t0)
         host_t["ingest_call"].append(h1 - t1)
@@ -567,6 +728,7 @@ def main():
     if world > 1:
         dist.barrier()
     wall1 = time.time()
+    pool.set_timing(False)
     t_ingest = [ev[i][0].elapsed_time(ev[i][1]) / 1e3 for i in range(args.steps)]
     t_close = [ev[i][1].elapsed_time(ev[i][2]) / 1e3 for i in range(args.steps)]
 
@@ -574,39 +736,161 @@ def main():
     # device (asse_ingest returns once the buffer has been read) -> ingest ->
     # close -> report on the host; as in the device-timed loop, the next
     # slice's pairs go in before the report of this one is read
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    e2e_pairs, d2h = 0, 0
-    pool.ingest(pinned[args.warmup % n_cycled])
-    for i in range(args.steps):
-        j = (args.warmup + i) % n_cycled
-        pool.close_slice(w.k)
-        if i + 1 < args.steps:
-            pool.ingest(pinned[(args.warmup + i + 1) % n_cycled])
-        rep = pool.report()
-        e2e_pairs += n_pairs[j]
-        d2h += rep.nbytes + 32
-    torch.cuda.synchronize()
-    e2e_elapsed = time.perf_counter() - t0
-    clk = clocks.stop(wall0, wall1)
+    e2e_pairs, d2h, e2e_elapsed = 0, 0, None
+    if with_e2e:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        pool.ingest(pinned[args.warmup % n_cycled])
+        for i in range(args.steps):
+            j = (args.warmup + i) % n_cycled
+            pool.close_slice(w.k)
+            if i + 1 < args.steps:
+                pool.ingest(pinned[(args.warmup + i + 1) % n_cycled])
+            rep = pool.report()
+            e2e_pairs += n_pairs[j]
+            d2h += rep.nbytes + 32
+        torch.cuda.synchronize()
+        e2e_elapsed = time.perf_counter() - t0
     breakdown = stepwise_breakdown(pool, dev, w, args.warmup) if args.breakdown else None
     sector = random_sector_rate(pool, stream)
+    used = [(args.warmup + i) % n_cycled for i in range(args.steps)]
+    info = pool.info()
+    pool.close()
+    return dict(elapsed=elapsed, e2e_elapsed=e2e_elapsed, pairs_done=pairs_done, e2e_pairs=e2e_pairs, d2h=d2h,
+                t_ingest=t_ingest, t_close=t_close, t_scan=t_scan, t_restore=t_restore, lat=lat, host_t=host_t,
+                launches=launches, n_reported=n_reported, wall=(wall0, wall1), breakdown=breakdown, sector=sector,
+                used=used, n_pairs=n_pairs, n_distinct=n_distinct, host=host, info=info, n_cycled=n_cycled)
 
+
+def summarize(w, args, m) -> dict:
+    """Kernel times, latencies and the rooflines of the ingest and the scan."""
+    ing = statistics.mean(m["t_ingest"])
+    scan = statistics.mean(m["t_scan"])
+    used = m["used"]
+    peak, peak_src = peaks()
+    alg_ing = statistics.mean(8 * m["n_pairs"][j] + 32 * w.r * m["n_distinct"][j] for j in used)
+    alg_scan = scan_alg_bytes(w, m["info"], args.counter)
+    r_ing = roofline_entry("ingest", alg_ing, ing, peak, peak_src,
+                           "8 B per pair + 32 B x r per distinct (aip, bip) pair", w.name, args.counter)
+    r_ing["distinct_pair_fraction"] = statistics.mean(m["n_distinct"][j] / m["n_pairs"][j] for j in used)
+    r_scan = roofline_entry("scan", alg_scan, scan, peak, peak_src,
+                            "the pool read once + the refreshed words written (Algorithm 2)", w.name, args.counter)
+    lat_ms = sorted(1e3 * x for x in m["lat"])
+    sector = m["sector"]
+    return {
+        "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * statistics.mean(m["t_close"]), "scan": 1e3 * scan,
+                      "restore": 1e3 * statistics.mean(m["t_restore"]),
+                      "ingest_p50": 1e3 * statistics.median(m["t_ingest"]),
+                      "close_p50": 1e3 * statistics.median(m["t_close"]),
+                      "what": "CUDA events on the pool's stream: around each ingest and close call, and recorded by "
+                              "the library around the scan and the restore kernel of each close"},
+        "slice_latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                                 int(0.99 * len(lat_ms)))],
+                             "what": "close_slice call to report on the host (the next slice's ingest is "
+                                     "queued in between)"},
+        "rooflines": {"ingest": r_ing, "scan": r_scan},
+        "random_sector_roofline": {
+            "peak": sector["gbs"], "unit": "GB/s", "frac": r_ing["achieved"] / sector["gbs"],
+            "reads_per_s": sector["reads_per_s"],
+            "what": "random 4-byte reads of this pool's words (one 32-byte sector each, every SM busy), "
+                    "timed in this run (pool of %d MB, L2 of %d MB); the ingest's algorithmic bytes per launch "
+                    "over its time, against this rate" % (sector["pool_bytes"] >> 20, sector["l2_bytes"] >> 20)},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="long", choices=["tiny_b", "link", "long"],
+                    help="the headline workload (default: the long window, k=60, 32 Mi pairs per slice)")
+    ap.add_argument("--secondary", default="link", choices=["link", "none"],
+                    help="a second workload measured in the same run and reported under its own key")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--breakdown", action="store_true", help="also time scan / restore / refresh separately")
+    ap.add_argument("--mode", default="slice", choices=["slice", "serve", "learned", "accuracy"],
+                    help="slice: one pool, the headline line; serve: the multi-stream serving loop; "
+                         "learned: per-slice learned inference (features + tensor-core MLP); accuracy: FPR/FNR of "
+                         "the sliding pool (Eq. 4 and the learned candidate model) and of the 1-bit discrete mode "
+                         "at equal memory, on exact window cardinalities")
+    ap.add_argument("--acc-slices", type=int, default=0, help="accuracy mode: slices to run (0: 3k, or k+3 for the "
+                                                              "long workload)")
+    ap.add_argument("--serve-slices", type=int, default=12)
+    ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
+    ap.add_argument("--cycled", type=int, default=0,
+                    help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
+    ap.add_argument("--key-table", default="auto", choices=["auto", "on", "off"],
+                    help="the ingest's slice-wide key table (auto: for pools larger than L2)")
+    ap.add_argument("--clocks-dir", default="", help="where the nvidia-smi clock samples of the timed region go "
+                                                      "(default: the temporary directory)")
+    ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned"],
+                    help="at: the paper's asynchronous timestamps; ace: aging counters; aligned: timestamps with "
+                         "one ACT per ATV (whole-pool refresh every k slices)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.mode in ("serve", "learned", "accuracy"):
+        if rank == 0:
+            {"serve": run_serve, "learned": run_learned, "accuracy": run_accuracy}[args.mode](args)
+        return
+    w = synth.workload(args.workload, seed=1 + rank)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    w2 = None
+    if args.secondary != "none" and args.secondary != args.workload:
+        w2 = synth.workload(args.secondary, seed=1 + rank)
+
+    # every input slice is generated up front, in host processes started with
+    # spawn before any CUDA call of this process
+    pre = {}
+    for wl in (w, w2):
+        if wl is not None:
+            nc = args.cycled or (N_SLICES_CYCLED if wl.n_per_slice <= (8 << 20) else 4)
+            pre[wl.name] = make_slices(wl, nc)
+    args.slices_of = lambda wl, n: pre[wl.name]
+
+    import torch
+    from paper_1807_01527_gb300 import asse, build
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    stream = torch.cuda.current_stream()
+
+    clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), "bench_clocks_%d.csv" % rank), local)
+    m = bench_workload(w, args, world, rank, stream, torch, asse, dist)
+    clk = clocks.stop(*m["wall"])
+    m2 = bench_workload(w2, args, world, rank, stream, torch, asse, dist) if w2 is not None else None
+
+    elapsed, e2e_elapsed, pairs_done, e2e_pairs = m["elapsed"], m["e2e_elapsed"], m["pairs_done"], m["e2e_pairs"]
     if world > 1:
         elapsed, e2e_elapsed, pairs_done, e2e_pairs = reduce_over_ranks([elapsed, e2e_elapsed],
                                                                         [pairs_done, e2e_pairs], "cuda")
+    second = None
+    if m2 is not None:
+        el2, pd2 = m2["elapsed"], m2["pairs_done"]
+        ee2, ep2 = m2["e2e_elapsed"], m2["e2e_pairs"]
+        if world > 1:
+            el2, ee2, pd2, ep2 = reduce_over_ranks([el2, ee2], [pd2, ep2], "cuda")
+        second = dict(summarize(w2, args, m2), value=pd2 / el2, unit="pkts/s",
+                      ms_per_step=1e3 * el2 / args.steps, config=workload_desc(w2),
+                      e2e={"value": ep2 / ee2, "unit": "pkts/s",
+                           "h2d_bytes_per_step": int(8 * statistics.mean(m2["n_pairs"])),
+                           "d2h_bytes_per_step": int(m2["d2h"] / args.steps)})
 
     if rank == 0:
-        ing = statistics.mean(t_ingest)
-        cls = statistics.mean(t_close)
-        n_avg = statistics.mean(n_pairs)
-        used = [(args.warmup + i) % n_cycled for i in range(args.steps)]
-        alg_bytes = statistics.mean(8 * n_pairs[j] + 32 * w.r * n_distinct[j] for j in used)
-        peak, peak_src = peaks()
-        achieved = alg_bytes / ing / 1e9
-        lat_ms = sorted(1e3 * x for x in lat)
+        summ = summarize(w, args, m)
+        rl = summ.pop("rooflines")
+        dominant = max(rl, key=lambda k: rl[k]["ms_per_launch"])
         line = {
             "metric": METRIC, "value": pairs_done / elapsed, "unit": "pkts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -615,44 +899,29 @@ def main():
             "config": dict(workload_desc(w), counter=args.counter.upper(), key_table=args.key_table,
                            parallelism="replicas" if world > 1 else "single",
                            l2="inputs cycle over %d distinct slices (%d MB) held in HBM, more than L2; the pool "
-                              "state stays resident across steps" % (n_cycled, sum(p.nbytes for p in host) >> 20)),
-            "slice_latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
-                                                                                     int(0.99 * len(lat_ms)))],
-                                 "what": "close_slice call to report on the host (the next slice's ingest is "
-                                         "queued in between)"},
-            "kernel_ms": {"ingest": 1e3 * ing, "close": 1e3 * cls,
-                          "ingest_p50": 1e3 * statistics.median(t_ingest), "close_p50": 1e3 * statistics.median(t_close),
-                          "what": "CUDA events on the pool's stream around each call; an ingest recorded right "
-                                  "after the host waited for a report also holds its launch latency"},
-            "host_call_ms_p50": {k: 1e3 * statistics.median(v) for k, v in host_t.items()},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": INGEST_TRAFFIC.get((args.workload, args.counter), (None, None))[0],
-                         "traffic_source": INGEST_TRAFFIC.get((args.workload, args.counter), (None, None))[1],
-                         "kernel": "ingest",
-                         "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
-                         "model": "8 B per pair + 32 B x r per distinct (aip, bip) pair",
-                         "distinct_pair_fraction": statistics.mean(n_distinct[j] / n_pairs[j] for j in used)},
-            "random_sector_roofline": {
-                "peak": sector["gbs"], "unit": "GB/s", "frac": achieved / sector["gbs"],
-                "reads_per_s": sector["reads_per_s"],
-                "what": "random 4-byte reads of this pool's words (one 32-byte sector each, every SM busy), "
-                        "timed in this run (pool of %d MB, L2 of %d MB); the ingest's algorithmic bytes per launch "
-                        "over its time, against this rate" % (sector["pool_bytes"] >> 20, sector["l2_bytes"] >> 20)},
+                              "state stays resident across steps" % (m["n_cycled"],
+                                                                     sum(p.nbytes for p in m["host"]) >> 20)),
+            "roofline": dict(rl[dominant], dominant=True),
+            "roofline_other": {k: v for k, v in rl.items() if k != dominant},
             "e2e": {"value": e2e_pairs / e2e_elapsed, "unit": "pkts/s",
-                    "h2d_bytes_per_step": int(8 * n_avg), "d2h_bytes_per_step": int(d2h / args.steps)},
-            "gpu_launches": int(launches),
-            "reported_per_slice": n_reported / args.steps,
+                    "h2d_bytes_per_step": int(8 * statistics.mean(m["n_pairs"])),
+                    "d2h_bytes_per_step": int(m["d2h"] / args.steps)},
+            "gpu_launches": int(m["launches"]),
+            "reported_per_slice": m["n_reported"] / args.steps,
+            "host_call_ms_p50": {k: 1e3 * statistics.median(v) for k, v in m["host_t"].items()},
             "clocks": clk,
         }
-        if breakdown:
-            line["breakdown_ms"] = breakdown
+        line.update(summ)
+        if m["breakdown"]:
+            line["breakdown_ms"] = m["breakdown"]
+        if second is not None:
+            line[w2.name] = second
         if not args.no_cpu_baseline and world == 1:
-            per_slice, text, n = oracle_slice_time(w, args.ref_sample, args.counter)
-            line["cpu_baseline"] = {"value": n / per_slice, "unit": "pkts/s", "cores": 1, "kind": "oracle",
+            p0 = m["host"][0]
+            dt, cores, text, _ = oracle_slice_time(w, p0, args.counter)
+            line["cpu_baseline"] = {"value": p0.shape[0] / dt, "unit": "pkts/s", "cores": cores, "kind": "oracle",
                                     "sample": text}
         print(json.dumps(line), flush=True)
-    pool.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -118,13 +118,16 @@ typedef struct asse_config {
 typedef struct asse_superpoint {
     uint32_t aip;   /* restored host address */
     uint32_t nat;   /* NAT(aip), Algorithm 5 */
-    float est;      /* Eq. 4 estimate (evaluated in FP64, stored FP32); +inf if saturated */
+    float est;      /* Eq. 4 estimate, stored FP32: evaluated in FP32 where an error bound keeps
+                     * it within 8e-6 relative of the FP64 value, else in FP64; +inf if saturated */
     uint32_t flags; /* ASSE_SP_* */
 } asse_superpoint;
 
 /* Derived layout of a pool, for callers that read the packed state. */
 typedef struct asse_pool_info {
-    uint32_t w;          /* bits per counter: ceil(log2(2k+1)) (AT) or ceil(log2(k+1)) (ACE) */
+    uint32_t w;          /* bits per packed counter field: ceil(log2(2k+1)) (AT) or ceil(log2(k+1))
+                          * (ACE), except 8 where that is 7 (four byte-wide fields per word, as many
+                          * as 7-bit fields would give; the top bit of each byte stays 0) */
     uint32_t fields;     /* counters per 32-bit word: floor(32/w); field j at bits [j*w, j*w+w) */
     uint32_t words;      /* 32-bit words per ATV, ceil(g/fields) rounded up to a multiple of 8 */
     uint32_t E;          /* ATVs per row: 2^(c+u); ATV index in a row = (frame << c) | column */
@@ -204,17 +207,18 @@ ASSE_API int asse_restore(asse_pool *pool);
 /* Size of the fixed restore scratch of asse_restore_static, in column tuples. */
 #define ASSE_STATIC_RESTORE_TUPLES 131072u
 
-/* The restore of asse_restore (Algorithm 4, Algorithm 5 and Eq. 4 on the
- * super ATVs of the last scan), for callers that cannot allocate device
- * memory while they run it.  This entry point has no counterpart in the
- * paper.  A slice-closing loop with a latency budget cannot call cudaMalloc
- * or cudaFree, since those may synchronise the device and stall the streams
- * that feed it, and some hosts give all device memory to another allocator
- * at start-up so that nothing may be allocated later.  This call allocates
- * nothing and calls no allocating routine: the join's partial column tuples
- * live in one array of ASSE_STATIC_RESTORE_TUPLES tuples (3 MiB) compiled
- * into the library, which every GPU that loads the library holds until the
- * process exits.
+/* No counterpart in the paper: the restore of asse_restore, for callers that
+ * cannot allocate device memory while they run it.  A slice-closing loop with
+ * a latency budget cannot call cudaMalloc or cudaFree, since those may
+ * synchronise the device and stall the streams that feed it, and some hosts
+ * give all device memory to another allocator at start-up so that nothing may
+ * be allocated later.  This call allocates nothing and calls no allocating
+ * routine: the join's partial column tuples live in one array of
+ * ASSE_STATIC_RESTORE_TUPLES tuples (3 MiB) compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ * It restores the window selected by asse_select_window (window 0 after a
+ * scan or a single-window close) from the outputs of the last scan or close.
  *
  *  tuples_per_frame  tuples kept per frame and join level (the role of
  *                    restore_cap); tuples_per_frame * 2 * 2^u must not exceed
@@ -301,6 +305,20 @@ ASSE_API int asse_load(asse_pool *pool, const void *src, uint64_t n);
  * traffic is r random words per pair new to the slice.  Does not
  * synchronise.  Errors: EINVAL, ECUDA. */
 ASSE_API int asse_probe_random_reads(asse_pool *pool, uint64_t n_reads, uint64_t *n_issued);
+
+/* Measurement aid, no counterpart in the paper: with on != 0, every later
+ * asse_close_slice records CUDA events on the pool's stream before and after
+ * its scan kernel and after its restore kernel (the work of the close that
+ * runs on the device), for asse_close_timing.  on = 0 stops recording.
+ * Errors: ECUDA (event creation). */
+ASSE_API int asse_set_timing(asse_pool *pool, int on);
+
+/* Device time of the last asse_close_slice recorded with timing on, in
+ * milliseconds: ms[0] the scan (Algorithm 1 counts, loads, super ATVs and the
+ * fused Algorithm 2 refresh), ms[1] the restore (Algorithms 4-5, Eq. 4 and
+ * the opening of the next slice).  Waits for that close.  Errors: EINVAL
+ * (NULL), ESTATE (no timed close since timing was turned on), ECUDA. */
+ASSE_API int asse_close_timing(asse_pool *pool, float *ms);
 
 /* Number of kernels this pool has launched since creation. */
 ASSE_API uint64_t asse_launches(const asse_pool *pool);

@@ -60,10 +60,11 @@ ASSE_API int asse_features(asse_pool *pool, uint16_t *x_dev);
 
 /* Learned cardinality estimate of every ATV of a pool, for the window of
  * the last asse_scan: the feature rows (written to x_dev, [r*E][ASSE_FEAT]
- * bf16, 16-byte aligned), the model on them, and est_dev[i] = exp(model) where
- * the model is inside its training range (the ATV not saturated and
- * 0 <= model <= max_log_n, the log of the largest cardinality it was trained
- * on), else Eq. 2's linear-counting estimate from the ATV's count (a
+ * bf16, 16-byte aligned), the model on them, and est_dev[i] =
+ * exp(max(model, 0)) where the ATV holds an active AT and the model is
+ * inside its training range (model <= max_log_n, the log of the largest
+ * cardinality it was trained on; a host has at least one bip), else Eq. 2's
+ * linear-counting estimate from the ATV's count (0 for an empty ATV, a
  * saturated count g taken as g - 1/2).  *n_fallback_dev (device) receives
  * the number of ATVs that fell back to Eq. 2.  The model must run on the
  * pool's stream.  Same validity window as asse_features.
@@ -77,6 +78,35 @@ ASSE_API int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log
  * buffers; stream-ordered on stream.  Errors: EINVAL, ECUDA. */
 ASSE_API int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uint16_t *x_dev,
                                float *log_n_dev, float *lc_dev, void *stream);
+
+/* Learned estimate of a candidate super point, in place of Eq. 4 (Sec. 4.3):
+ * the same MLP (a separate instance) fed a feature row of the candidate
+ * host built from its r ATVs instead of one ATV:
+ *   [0]        NAT / g, the ATs active in all r ATVs (Algorithm 5)
+ *   [1 + a]    ATs active in all r ATVs whose oldest timestamp over the rows
+ *              is a slices old, / g (a < k' <= 64): the host sets all r ATs
+ *              of a bip in the same slice, other hosts only make some younger
+ *   [65]       UP of the host's frame (the product of the row loads, Eq. 4)
+ *   [66], [67] the smallest and the largest row load P_i
+ *   [68 + i]   |ATV_i|^{k'} / g of the host's ATV in row i (r <= 8)
+ * Target: ln(cardinality). */
+
+/* Candidate feature rows of n hosts (aips_dev, device) of a pool, for the
+ * window and loads of the last asse_scan, into x_dev ([n][ASSE_FEAT] bf16,
+ * device).  Same validity window as asse_features.
+ * Errors: ESTATE, EINVAL, ECUDA. */
+ASSE_API int asse_candidate_features(asse_pool *pool, const uint32_t *aips_dev, uint64_t n, uint16_t *x_dev);
+
+/* Synthetic candidate states first .. first+n-1: one host of cardinality n
+ * (log-uniform in [1, 2^n_max_log2], spread over the k slices with random
+ * shares) in r ATVs, each row with its own background (every AT set in each
+ * slice with a probability p_i drawn in [0, bg_max] per state and row); the
+ * row loads are P_i = 1 - (1 - p_i)^k.  Outputs (device): feature rows x_dev
+ * [n][ASSE_FEAT] bf16, log_n_dev [n] = ln(n), and eq4_dev [n], Eq. 4's
+ * estimate from the state's NAT and UP (+inf when saturated).  cfg->r <= 8.
+ * Stream-ordered on stream.  Errors: EINVAL, ECUDA. */
+ASSE_API int asse_synth_candidates(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uint16_t *x_dev,
+                                   float *log_n_dev, float *eq4_dev, void *stream);
 
 /* A model with Kaiming-uniform weights drawn from seed and zero biases. */
 ASSE_API int asse_mlp_create(uint64_t seed, void *stream, asse_mlp **out);
@@ -100,9 +130,24 @@ ASSE_API int asse_mlp_forward(asse_mlp *mlp, const uint16_t *x_dev, uint64_t n, 
  * up a bounded wait (its outputs are then invalid). */
 ASSE_API int asse_mlp_check(asse_mlp *mlp);
 
-/* Gradients of the mean squared error (1/n) sum (model(x_i) - t_i)^2 with
- * respect to every parameter, for n rows (device buffers); loss_dev (may be
- * NULL) receives the loss.  Does not change the parameters. */
+/* Training losses over n rows with targets t_i = ln(cardinality):
+ *   ASSE_LOSS_LOG_MSE  (1/n) sum (model(x_i) - t_i)^2, the squared error of
+ *                      the log-estimate (default);
+ *   ASSE_LOSS_REL_MSE  (1/n) sum (exp(model(x_i) - t_i) - 1)^2, the squared
+ *                      relative error of the estimate exp(model) (model - t
+ *                      clamped at 20), which favours the estimate with the
+ *                      lowest relative error where a state says little
+ *                      about its cardinality (a saturated estimator). */
+#define ASSE_LOSS_LOG_MSE 0
+#define ASSE_LOSS_REL_MSE 1
+
+/* Select the loss of later asse_mlp_backward / asse_mlp_train_step calls.
+ * Errors: EINVAL. */
+ASSE_API int asse_mlp_set_loss(asse_mlp *mlp, int kind);
+
+/* Gradients of the selected loss with respect to every parameter, for n rows
+ * (device buffers); loss_dev (may be NULL) receives the loss.  Does not
+ * change the parameters. */
 ASSE_API int asse_mlp_backward(asse_mlp *mlp, const uint16_t *x_dev, const float *t_dev, uint64_t n,
                                float *loss_dev);
 

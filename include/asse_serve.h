@@ -13,6 +13,7 @@
 #define ASSE_SERVE_H
 
 #include "asse.h"
+#include "asse_learn.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -75,6 +76,32 @@ ASSE_API int asse_server_sync(asse_server *srv);
 /* Close stream id: wait for its work, free its pool and memory (returned to
  * the budget).  Unpolled reports are dropped. */
 ASSE_API int asse_server_close(asse_server *srv, uint32_t id);
+
+/* Not in the paper: learned per-ATV inference in the serving loop.  Attach
+ * the model mlp to stream id: from its next close on, the close graph runs,
+ * between the scan and the refresh (which would change the state the
+ * features read), the feature rows of every ATV, the tensor-core MLP and the
+ * rule of asse_estimate_learned (exp(model) inside [0, max_log_n] and for an
+ * unsaturated ATV, else Eq. 2 from its count), then the restore, the refresh
+ * and the next slice, so the close-to-report latency includes the inference.
+ * The estimates stay in device memory, one buffer per report slot.  The
+ * stream must have no close in flight (EAGAIN: poll first); its close graphs
+ * are captured again (synchronises).  The feature rows and estimate buffers
+ * are charged to the budget (ENOMEM if they do not fit; the stream is then
+ * unchanged).  The model is only read and must outlive the stream; one model
+ * may serve several streams.  On ECUDA the stream is closed.
+ * Errors: EINVAL (kp > 64, a model already attached), EAGAIN, ENOMEM, ECUDA. */
+ASSE_API int asse_server_attach_model(asse_server *srv, uint32_t id, asse_mlp *mlp, float max_log_n);
+
+/* Copy the learned estimates of the close that the last successful
+ * asse_server_poll of stream id returned into out (host or device, `where`):
+ * r*E floats in ATV order (row-major: row i, then the ATV index); *n_fallback
+ * (may be NULL) receives how many fell back to Eq. 2.  Available until
+ * ASSE_SERVE_RING further closes of the stream have been submitted.
+ * Synchronises the stream.  Errors: EINVAL, ESTATE (no model attached or
+ * nothing polled yet), ECAPACITY (cap < r*E), ECUDA. */
+ASSE_API int asse_server_estimates(asse_server *srv, uint32_t id, float *out, uint64_t cap, int where,
+                                   uint32_t *n_fallback);
 
 /* The pool of stream id (for reading its state), or NULL. */
 ASSE_API asse_pool *asse_server_pool(asse_server *srv, uint32_t id);

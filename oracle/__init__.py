@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         # -ffp-contract=off: no fused multiply-add, so Eq. 2/Eq. 4 round each
         # operation exactly as written on every host architecture.
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-pthread",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -87,6 +87,12 @@ def lib():
             "oracle_eq4": (dbl, [u32, u32, dbl]),
             "oracle_eq2": (dbl, [u32, u32]),
             "oracle_estimate": (dbl, [vp, vp, u32, u32, vp]),
+            "oracle_cores": (ctypes.c_int, []),
+            "oracle_ingest_mt": (None, [vp, vp, u64, ctypes.c_int]),
+            "oracle_advance_mt": (None, [vp, ctypes.c_int]),
+            "oracle_counts_mt": (None, [vp, u32, vp, ctypes.c_int]),
+            "oracle_restore_mt": (i64, [vp, vp, vp, i64, i64, ctypes.c_int]),
+            "oracle_estimate_mt": (None, [vp, vp, vp, u64, u32, vp, vp, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -118,6 +124,11 @@ def eq2(g: int, cnt: int) -> float:
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def cores() -> int:
+    """Host cores the multi-threaded oracle calls use by default."""
+    return int(lib().oracle_cores())
 
 
 class Oracle:
@@ -186,22 +197,33 @@ class Oracle:
         return int(lib().oracle_act(self._st, h))
 
     # -- slice operations
-    def ingest(self, pairs: np.ndarray):
-        """Algorithm 3 over an (n, 2) uint32 array of (aip, bip) pairs."""
+    def ingest(self, pairs: np.ndarray, threads: int = 1):
+        """Algorithm 3 over an (n, 2) uint32 array of (aip, bip) pairs; with
+        threads != 1 the same arithmetic on that many threads (0: every
+        core), split by (row, frame)."""
         pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
-        lib().oracle_ingest(self._st, _ptr(pairs), pairs.shape[0])
+        if threads == 1:
+            lib().oracle_ingest(self._st, _ptr(pairs), pairs.shape[0])
+        else:
+            lib().oracle_ingest_mt(self._st, _ptr(pairs), pairs.shape[0], threads)
 
-    def advance(self):
+    def advance(self, threads: int = 1):
         """Close the open slice and open the next (refresh of Algorithm 2)."""
-        lib().oracle_advance(self._st)
+        if threads == 1:
+            lib().oracle_advance(self._st)
+        else:
+            lib().oracle_advance_mt(self._st, threads)
 
     def active(self, row: int, est: int, h: int, kp: int) -> bool:
         return bool(lib().oracle_active(self._st, row, est, h, kp))
 
-    def counts(self, kp: int) -> np.ndarray:
+    def counts(self, kp: int, threads: int = 1) -> np.ndarray:
         """|ATV|^{k'} per ATV, shape [r][E]."""
         cnt = np.zeros((self.r, self.E), dtype=np.uint32)
-        lib().oracle_counts(self._st, kp, _ptr(cnt))
+        if threads == 1:
+            lib().oracle_counts(self._st, kp, _ptr(cnt))
+        else:
+            lib().oracle_counts_mt(self._st, kp, _ptr(cnt), threads)
         return cnt
 
     def aat(self, cnt: np.ndarray) -> np.ndarray:
@@ -246,19 +268,46 @@ class Oracle:
         v = float(lib().oracle_estimate(self._st, _ptr(aat), aip, kp, _ptr(nat)))
         return v, int(nat[0])
 
+    def restore_mt(self, cnt: np.ndarray, cap: int, frame_cap: int, threads: int = 0):
+        """Algorithm 4 with the frames spread over threads (no stop rule;
+        each frame keeps up to frame_cap candidates).  Returns (number of
+        candidates, the first min(n, cap) in frame order)."""
+        cnt = np.ascontiguousarray(cnt, dtype=np.uint32)
+        out = np.zeros(max(cap, 1), dtype=np.uint32)
+        n = int(lib().oracle_restore_mt(self._st, _ptr(cnt), _ptr(out), cap, frame_cap, threads))
+        return n, out[: min(n, cap)].copy()
+
+    def estimate_many(self, aat: np.ndarray, aips: np.ndarray, kp: int, threads: int = 0):
+        """(Eq. 4 estimates, NAT) of many hosts, on threads."""
+        aat = np.ascontiguousarray(aat, dtype=np.uint64)
+        aips = np.ascontiguousarray(aips, dtype=np.uint32)
+        est = np.zeros(aips.size, dtype=np.float64)
+        nat = np.zeros(aips.size, dtype=np.uint32)
+        lib().oracle_estimate_mt(self._st, _ptr(aat), _ptr(aips), aips.size, kp, _ptr(est), _ptr(nat), threads)
+        return est, nat
+
     # -- the whole close of one slice (Sec. 4.2-4.3), before the refresh
-    def close_report(self, kp: int, cap: int = 1 << 22, limit_extra: int = -1):
+    def close_report(self, kp: int, cap: int = 1 << 22, limit_extra: int = -1, threads: int = 1):
         """Counts, loads, candidates, NAT and Eq. 4 for the window ending at the
         open slice.  Returns a dict; 'report' holds (aip, est, nat) rows with
-        est >= theta, sorted by aip.  Does not advance the slice."""
-        cnt = self.counts(kp)
+        est >= theta, sorted by aip.  Does not advance the slice.  threads !=
+        1 runs the same steps on that many threads (0: every core); the
+        restore then has no stop rule and keeps up to cap candidates per
+        frame."""
+        cnt = self.counts(kp, threads)
         aat = self.aat(cnt)
-        n, cand = self.restore(cnt, cap, limit_extra)
         rows = []
-        if n <= cap:
-            for aip in cand.tolist():
-                est, nat = self.estimate(aat, aip, kp)
-                rows.append((aip, est, nat))
+        if threads == 1:
+            n, cand = self.restore(cnt, cap, limit_extra)
+            if n <= cap:
+                for aip in cand.tolist():
+                    est, nat = self.estimate(aat, aip, kp)
+                    rows.append((aip, est, nat))
+        else:
+            n, cand = self.restore_mt(cnt, cap, cap, threads)
+            if n <= cap:
+                est, nat = self.estimate_many(aat, cand, kp, threads)
+                rows = [(int(a), float(e), int(m)) for a, e, m in zip(cand.tolist(), est.tolist(), nat.tolist())]
         rows.sort()
         report = [row for row in rows if row[1] >= self.theta]
         return {"counts": cnt, "aat": aat, "n_candidates": n, "candidates": rows, "report": report}

@@ -356,32 +356,31 @@ static void place(const oracle_state *st, uint32_t i, uint32_t xi, uint32_t *val
  * (in frame order, then tuple order) and returns how many there are.  The
  * enumeration stops once more than cap+limit_extra candidates were seen;
  * limit_extra < 0 means never stop. */
-int64_t oracle_restore(const oracle_state *st, const uint32_t *cnt, uint32_t *out, int64_t cap,
-                       int64_t limit_extra)
+/* Algorithm 4 on frame j alone.  Writes up to cap candidates to out, counts
+ * every candidate of the frame into *n_out (which holds the candidates of
+ * the frames before, so the stop rule sees the running total), and returns 1
+ * if the enumeration stopped because *n_out exceeded cap + limit_extra
+ * (limit_extra < 0: never).  out and cap are relative to this frame. */
+static int restore_frame(const oracle_state *st, const uint32_t *cnt, uint32_t j, uint32_t *out, int64_t cap,
+                         int64_t *n_out, int64_t base, int64_t limit)
 {
-    uint32_t r = st->p.r, nf = 1u << st->p.u, cols = 1u << st->p.c;
+    uint32_t r = st->p.r, cols = 1u << st->p.c;
     uint32_t T = oracle_threshold(st);
-    uint32_t **sa = (uint32_t **)calloc(r, sizeof(uint32_t *));
-    uint32_t *nsa = (uint32_t *)calloc(r, sizeof(uint32_t));
-    uint32_t *val = (uint32_t *)calloc(r, sizeof(uint32_t));
-    uint32_t *msk = (uint32_t *)calloc(r, sizeof(uint32_t));
-    uint32_t *idx = (uint32_t *)calloc(r, sizeof(uint32_t));
+    uint32_t *sa[32];
+    uint32_t nsa[32], val[32], msk[32], idx[32];
+    int stop = 0, empty = 0;
     for (uint32_t i = 0; i < r; i++)
         sa[i] = (uint32_t *)malloc(sizeof(uint32_t) * cols);
-    int64_t n_out = 0;
-    for (uint32_t j = 0; j < nf; j++) {
-        /* SA(i, j): super ATVs of row i in frame j, by column index. */
-        int empty = 0;
-        for (uint32_t i = 0; i < r; i++) {
-            nsa[i] = 0;
-            for (uint32_t x = 0; x < cols; x++)
-                if (cnt[(size_t)i * st->E + (((size_t)j << st->p.c) | x)] >= T)
-                    sa[i][nsa[i]++] = x;
-            if (nsa[i] == 0)
-                empty = 1;
-        }
-        if (empty)
-            continue;
+    /* SA(i, j): super ATVs of row i in frame j, by column index. */
+    for (uint32_t i = 0; i < r; i++) {
+        nsa[i] = 0;
+        for (uint32_t x = 0; x < cols; x++)
+            if (cnt[(size_t)i * st->E + (((size_t)j << st->p.c) | x)] >= T)
+                sa[i][nsa[i]++] = x;
+        if (nsa[i] == 0)
+            empty = 1;
+    }
+    if (!empty) {
         for (uint32_t i = 0; i < r; i++)
             idx[i] = 0;
         for (;;) {
@@ -399,29 +398,47 @@ int64_t oracle_restore(const oracle_state *st, const uint32_t *cnt, uint32_t *ou
                 for (uint32_t i = 0; i < r; i++)
                     L |= val[i];
                 uint32_t y = (uint32_t)(((uint64_t)L << st->p.u) | j);
-                if (n_out < cap)
-                    out[n_out] = oracle_unmangle(st, y);
-                n_out++;
-                if (limit_extra >= 0 && n_out > cap + limit_extra)
-                    goto done;
+                int64_t k = *n_out - base;
+                if (k < cap)
+                    out[k] = oracle_unmangle(st, y);
+                (*n_out)++;
+                if (limit >= 0 && *n_out > limit) {
+                    stop = 1;
+                    break;
+                }
             }
             /* next tuple (odometer over the r rows) */
             uint32_t i = r;
+            int wrapped = 0;
             while (i > 0) {
                 i--;
                 if (++idx[i] < nsa[i])
                     break;
                 idx[i] = 0;
                 if (i == 0)
-                    goto frame_done;
+                    wrapped = 1;
             }
+            if (wrapped)
+                break;
         }
-    frame_done:;
     }
-done:
     for (uint32_t i = 0; i < r; i++)
         free(sa[i]);
-    free(sa); free(nsa); free(val); free(msk); free(idx);
+    return stop;
+}
+
+int64_t oracle_restore(const oracle_state *st, const uint32_t *cnt, uint32_t *out, int64_t cap,
+                       int64_t limit_extra)
+{
+    uint32_t nf = 1u << st->p.u;
+    int64_t n_out = 0;
+    int64_t limit = limit_extra >= 0 ? cap + limit_extra : -1;
+    for (uint32_t j = 0; j < nf; j++) {
+        int64_t base = n_out;
+        int64_t room = cap > base ? cap - base : 0;
+        if (restore_frame(st, cnt, j, out + (base < cap ? base : cap), room, &n_out, base, limit))
+            break;
+    }
     return n_out;
 }
 
@@ -492,4 +509,268 @@ double oracle_estimate(const oracle_state *st, const uint64_t *aat, uint32_t aip
     if (nat_out)
         *nat_out = nat;
     return oracle_eq4(st->p.g, nat, oracle_up(st, aat, z));
+}
+
+/* ------------------------------------------------------ all host cores */
+
+/* The same functions run on several threads, for the timed CPU baseline:
+ * the pool is split by (row, frame range), so no two threads write the same
+ * AT and no atomics are needed.  Each result equals the single-thread call's
+ * (the host tests compare them). */
+
+#include <pthread.h>
+#include <unistd.h>
+
+int oracle_cores(void)
+{
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n < 1 ? 1 : (int)n;
+}
+
+typedef struct {
+    oracle_state *st;
+    const uint32_t *pairs;
+    uint64_t lo, hi;        /* pair range (hash pass) */
+    uint32_t *z, *x, *h;    /* per pair: frame, r columns, BH */
+    uint32_t tid, nthreads; /* this thread's (row, frame) cells: every nthreads-th */
+    uint64_t n;
+    uint32_t kp;
+    const uint32_t *cnt;
+    uint32_t *cnt_out;
+    const uint64_t *aat;
+    const uint32_t *aips;
+    double *est;
+    uint32_t *nat;
+    uint32_t *frame_out;
+    int64_t frame_cap;
+    int64_t *frame_counts;
+} mt_job;
+
+typedef void *(*mt_fn)(void *);
+
+static void run_threads(mt_fn fn, mt_job *jobs, int nthreads)
+{
+    pthread_t th[256];
+    for (int t = 1; t < nthreads; t++)
+        pthread_create(&th[t], NULL, fn, &jobs[t]);
+    fn(&jobs[0]);
+    for (int t = 1; t < nthreads; t++)
+        pthread_join(th[t], NULL);
+}
+
+static int clamp_threads(int nthreads)
+{
+    if (nthreads < 1)
+        nthreads = oracle_cores();
+    return nthreads > 256 ? 256 : nthreads;
+}
+
+/* Hash pass of Algorithm 3: RRH(aip) and BH(bip) of a range of pairs. */
+static void *ingest_hash(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    uint32_t r = j->st->p.r, xx[32];
+    for (uint64_t q = j->lo; q < j->hi; q++) {
+        oracle_rrh(j->st, j->pairs[2 * q], xx, &j->z[q]);
+        for (uint32_t i = 0; i < r; i++)
+            j->x[q * r + i] = xx[i];
+        j->h[q] = oracle_bh(j->st, j->pairs[2 * q + 1]);
+    }
+    return NULL;
+}
+
+/* Set pass of Algorithm 3: the ATs of this thread's (row, frame) cells. */
+static void *ingest_set(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    oracle_state *st = j->st;
+    uint32_t r = st->p.r, nf = 1u << st->p.u;
+    for (uint64_t q = 0; q < j->n; q++) {
+        uint32_t z = j->z[q], h = j->h[q];
+        for (uint32_t i = 0; i < r; i++) {
+            if ((i * nf + z) % j->nthreads != j->tid)
+                continue;
+            uint32_t est = (z << st->p.c) | j->x[q * r + i];
+            uint32_t v = st->p.mode == 1 ? st->p.k : oracle_act(st, h);
+            st->at[at_index(st, i, est, h)] = (uint8_t)v;
+        }
+    }
+    return NULL;
+}
+
+/* oracle_ingest on nthreads threads (<= 0: every core), in chunks of pairs. */
+void oracle_ingest_mt(oracle_state *st, const uint32_t *pairs, uint64_t n, int nthreads)
+{
+    nthreads = clamp_threads(nthreads);
+    const uint64_t chunk = 1ull << 22;
+    uint32_t r = st->p.r;
+    uint32_t *z = (uint32_t *)malloc(sizeof(uint32_t) * chunk);
+    uint32_t *x = (uint32_t *)malloc(sizeof(uint32_t) * chunk * r);
+    uint32_t *h = (uint32_t *)malloc(sizeof(uint32_t) * chunk);
+    mt_job jobs[256];
+    for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
+        uint64_t m = n - c0 < chunk ? n - c0 : chunk;
+        for (int t = 0; t < nthreads; t++) {
+            memset(&jobs[t], 0, sizeof(mt_job));
+            jobs[t].st = st;
+            jobs[t].pairs = pairs + 2 * c0;
+            jobs[t].lo = m * (uint64_t)t / (uint64_t)nthreads;
+            jobs[t].hi = m * (uint64_t)(t + 1) / (uint64_t)nthreads;
+            jobs[t].z = z;
+            jobs[t].x = x;
+            jobs[t].h = h;
+            jobs[t].tid = (uint32_t)t;
+            jobs[t].nthreads = (uint32_t)nthreads;
+            jobs[t].n = m;
+        }
+        run_threads(ingest_hash, jobs, nthreads);
+        run_threads(ingest_set, jobs, nthreads);
+    }
+    free(z);
+    free(x);
+    free(h);
+}
+
+/* ATV ranges of (row, ATV) pairs: thread t takes ATVs [lo, hi) of the r*E. */
+static void *advance_range(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    oracle_state *st = j->st;
+    uint32_t k = st->p.k, g = st->p.g;
+    for (uint64_t a = j->lo; a < j->hi; a++) {
+        uint8_t *at = st->at + a * g;
+        for (uint32_t hh = 0; hh < g; hh++) {
+            if (st->p.mode == 1) {
+                if (at[hh] != 0)
+                    at[hh] -= 1;
+            } else {
+                at[hh] = (uint8_t)oracle_preserve_at(at[hh], oracle_act(st, hh), k);
+            }
+        }
+    }
+    return NULL;
+}
+
+/* oracle_advance on nthreads threads: the slice advances once, then each
+ * thread applies Algorithm 2 (or the ACE decrement) to its ATVs. */
+void oracle_advance_mt(oracle_state *st, int nthreads)
+{
+    nthreads = clamp_threads(nthreads);
+    uint64_t total = (uint64_t)st->p.r * st->E;
+    mt_job jobs[256];
+    st->t += 1;
+    for (int t = 0; t < nthreads; t++) {
+        memset(&jobs[t], 0, sizeof(mt_job));
+        jobs[t].st = st;
+        jobs[t].lo = total * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = total * (uint64_t)(t + 1) / (uint64_t)nthreads;
+    }
+    run_threads(advance_range, jobs, nthreads);
+}
+
+static void *counts_range(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    const oracle_state *st = j->st;
+    for (uint64_t a = j->lo; a < j->hi; a++) {
+        uint32_t row = (uint32_t)(a / st->E), e = (uint32_t)(a % st->E), n = 0;
+        for (uint32_t hh = 0; hh < st->p.g; hh++)
+            n += (uint32_t)oracle_active(st, row, e, hh, j->kp);
+        j->cnt_out[a] = n;
+    }
+    return NULL;
+}
+
+/* oracle_counts on nthreads threads (ATV ranges). */
+void oracle_counts_mt(oracle_state *st, uint32_t kp, uint32_t *cnt, int nthreads)
+{
+    nthreads = clamp_threads(nthreads);
+    uint64_t total = (uint64_t)st->p.r * st->E;
+    mt_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        memset(&jobs[t], 0, sizeof(mt_job));
+        jobs[t].st = st;
+        jobs[t].kp = kp;
+        jobs[t].cnt_out = cnt;
+        jobs[t].lo = total * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = total * (uint64_t)(t + 1) / (uint64_t)nthreads;
+    }
+    run_threads(counts_range, jobs, nthreads);
+}
+
+static void *restore_frames(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    uint32_t nf = 1u << j->st->p.u;
+    for (uint32_t f = j->tid; f < nf; f += j->nthreads) {
+        int64_t n = 0;
+        restore_frame(j->st, j->cnt, f, j->frame_out + (size_t)f * (size_t)j->frame_cap, j->frame_cap, &n, 0, -1);
+        j->frame_counts[f] = n;
+    }
+    return NULL;
+}
+
+/* oracle_restore (no stop rule) with the frames spread over threads: every
+ * frame's candidates (up to frame_cap each) are concatenated in frame order,
+ * which is the single-thread order.  Returns the total count; out receives
+ * the first cap. */
+int64_t oracle_restore_mt(oracle_state *st, const uint32_t *cnt, uint32_t *out, int64_t cap, int64_t frame_cap,
+                          int nthreads)
+{
+    nthreads = clamp_threads(nthreads);
+    uint32_t nf = 1u << st->p.u;
+    uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)nf * (size_t)(frame_cap > 0 ? frame_cap : 1));
+    int64_t *fn = (int64_t *)calloc(nf, sizeof(int64_t));
+    mt_job jobs[256];
+    int nt = nthreads < (int)nf ? nthreads : (int)nf;
+    for (int t = 0; t < nt; t++) {
+        memset(&jobs[t], 0, sizeof(mt_job));
+        jobs[t].st = st;
+        jobs[t].cnt = cnt;
+        jobs[t].tid = (uint32_t)t;
+        jobs[t].nthreads = (uint32_t)nt;
+        jobs[t].frame_out = buf;
+        jobs[t].frame_cap = frame_cap;
+        jobs[t].frame_counts = fn;
+    }
+    run_threads(restore_frames, jobs, nt);
+    int64_t n = 0;
+    for (uint32_t f = 0; f < nf; f++) {
+        int64_t m = fn[f] < frame_cap ? fn[f] : frame_cap;
+        for (int64_t i = 0; i < m; i++)
+            if (n + i < cap)
+                out[n + i] = buf[(size_t)f * (size_t)frame_cap + (size_t)i];
+        n += fn[f];
+    }
+    free(buf);
+    free(fn);
+    return n;
+}
+
+static void *estimate_range(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    for (uint64_t q = j->lo; q < j->hi; q++)
+        j->est[q] = oracle_estimate(j->st, j->aat, j->aips[q], j->kp, &j->nat[q]);
+    return NULL;
+}
+
+/* oracle_estimate of n hosts on nthreads threads. */
+void oracle_estimate_mt(oracle_state *st, const uint64_t *aat, const uint32_t *aips, uint64_t n, uint32_t kp,
+                        double *est, uint32_t *nat, int nthreads)
+{
+    nthreads = clamp_threads(nthreads);
+    mt_job jobs[256];
+    for (int t = 0; t < nthreads; t++) {
+        memset(&jobs[t], 0, sizeof(mt_job));
+        jobs[t].st = st;
+        jobs[t].aat = aat;
+        jobs[t].aips = aips;
+        jobs[t].kp = kp;
+        jobs[t].est = est;
+        jobs[t].nat = nat;
+        jobs[t].lo = n * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
+    }
+    run_threads(estimate_range, jobs, nthreads);
 }

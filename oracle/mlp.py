@@ -51,14 +51,22 @@ def forward(p: np.ndarray, X: np.ndarray, rounding: bool = True):
     return y, H1, H2
 
 
-def loss_and_grads(p: np.ndarray, X: np.ndarray, t: np.ndarray, rounding: bool = True):
+def loss_and_grads(p: np.ndarray, X: np.ndarray, t: np.ndarray, rounding: bool = True, loss: str = "log_mse"):
+    """Loss and gradients: 'log_mse' = mean (y - t)^2; 'rel_mse' = mean
+    (exp(y - t) - 1)^2 (y - t clamped at 20), the squared relative error of
+    exp(y) against exp(t)."""
     r = bf16 if rounding else _id
     q = unpack(p)
     n = X.shape[0]
     y, H1, H2 = forward(p, X, rounding)
     d = y - t
-    loss = float(np.mean(d * d))
-    dy = 2.0 * d / n
+    if loss == "rel_mse":
+        e = np.exp(np.minimum(d, 20.0))
+        dy = 2.0 * (e - 1.0) * e / n
+        loss = float(np.mean((e - 1.0) ** 2))
+    else:
+        dy = 2.0 * d / n
+        loss = float(np.mean(d * d))
     g = {"w3": H2.T @ dy, "b3": np.array([dy.sum()])}
     dZ2 = r(dy[:, None] * q["w3"][None, :] * (H2 > 0))
     g["b2"] = dZ2.sum(axis=0)
@@ -67,3 +75,32 @@ def loss_and_grads(p: np.ndarray, X: np.ndarray, t: np.ndarray, rounding: bool =
     g["b1"] = dZ1.sum(axis=0)
     g["W1"] = dZ1.T @ X
     return loss, pack(g), y
+
+
+def error_scales(p: np.ndarray, X: np.ndarray, t: np.ndarray, loss: str = "log_mse"):
+    """Per-entry scales for comparing a BF16-in / FP32-accumulate computation
+    of the network with this reference: for y and for every gradient entry,
+    the sum of the absolute values of the terms that make it up (with the
+    absolute values of the upstream factors).  Two implementations that
+    round the same BF16 storage points differ by at most a few BF16 steps
+    (2^-8 relative) of some of those terms, so |gpu - reference| stays
+    within a small multiple of 2^-8 times the scale, entry by entry.
+    Returns (scale of y [n], scale of the gradients [NPARAMS])."""
+    q = unpack(p)
+    n = X.shape[0]
+    y, H1, H2 = forward(p, X)
+    ys = np.abs(H2) @ np.abs(q["w3"]) + abs(q["b3"][0])
+    d = y - t
+    if loss == "rel_mse":
+        e = np.exp(np.minimum(d, 20.0))
+        ady = np.abs(2.0 * (e - 1.0) * e / n)
+    else:
+        ady = np.abs(2.0 * d / n)
+    s = {"w3": np.abs(H2).T @ ady, "b3": np.array([ady.sum()])}
+    A2 = ady[:, None] * np.abs(q["w3"])[None, :] * (H2 > 0)
+    s["b2"] = A2.sum(axis=0)
+    s["W2"] = A2.T @ np.abs(H1)
+    A1 = (A2 @ np.abs(bf16(q["W2"]))) * (H1 > 0)
+    s["b1"] = A1.sum(axis=0)
+    s["W1"] = A1.T @ np.abs(X)
+    return ys, pack(s)

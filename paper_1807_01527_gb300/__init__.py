@@ -6,4 +6,4 @@ of include/asse.h (libasse.so, built in-tree by ``build.build()``);
 ``asse.Pool`` is its Python binding.
 """
 from . import asse  # noqa: F401  (the binding loads libasse.so lazily)
-from .asse import AsseError, Pool, unpack_pool  # noqa: F401
+from .asse import AsseError, Pool  # noqa: F401

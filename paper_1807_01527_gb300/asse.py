@@ -72,6 +72,8 @@ EXPORTS = {
     "asse_snapshot": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
     "asse_load": (i32, [vp, vp, u64]),
     "asse_probe_random_reads": (i32, [vp, u64, ctypes.POINTER(u64)]),
+    "asse_set_timing": (i32, [vp, i32]),
+    "asse_close_timing": (i32, [vp, vp]),
     "asse_launches": (u64, [vp]),
     "asse_last_error": (ctypes.c_char_p, [vp]),
     "asse_strerror": (ctypes.c_char_p, [i32]),
@@ -79,6 +81,8 @@ EXPORTS = {
     "asse_features": (i32, [vp, vp]),
     "asse_estimate_learned": (i32, [vp, vp, ctypes.c_float, vp, vp, vp]),
     "asse_synth_states": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
+    "asse_candidate_features": (i32, [vp, vp, u64, vp]),
+    "asse_synth_candidates": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
     "asse_mlp_create": (i32, [u64, vp, ctypes.POINTER(vp)]),
     "asse_mlp_destroy": (None, [vp]),
     "asse_mlp_set_stream": (i32, [vp, vp]),
@@ -89,6 +93,7 @@ EXPORTS = {
     "asse_mlp_get_grads": (i32, [vp, vp]),
     "asse_mlp_train_step": (i32, [vp, vp, vp, u64, ctypes.c_float, vp]),
     "asse_mlp_check": (i32, [vp]),
+    "asse_mlp_set_loss": (i32, [vp, i32]),
     "asse_mlp_last_error": (ctypes.c_char_p, [vp]),
     # include/asse_serve.h
     "asse_server_create": (i32, [u64, ctypes.POINTER(vp)]),
@@ -101,6 +106,8 @@ EXPORTS = {
                                ctypes.POINTER(ctypes.c_float)]),
     "asse_server_sync": (i32, [vp]),
     "asse_server_close": (i32, [vp, u32]),
+    "asse_server_attach_model": (i32, [vp, u32, vp, ctypes.c_float]),
+    "asse_server_estimates": (i32, [vp, u32, vp, u64, i32, ctypes.POINTER(u32)]),
     "asse_server_pool": (vp, [vp, u32]),
     "asse_server_last_error": (ctypes.c_char_p, [vp]),
 }
@@ -148,16 +155,6 @@ def _pairs_arg(pairs):
         return pairs.data_ptr(), n, DEVICE if pairs.is_cuda else HOST, pairs
     a = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1)
     return a.ctypes.data, a.size // 2, HOST, a
-
-
-def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
-    """Packed pool words [r][E][words] -> counter values [r][E][g] (uint8):
-    field j of a word holds bits [j*w, j*w+w), AT h lives in word h // fields."""
-    w, F = info["w"], info["fields"]
-    words = words.reshape(-1, info["E"], info["words"])
-    h = np.arange(g)
-    sel = words[:, :, h // F]
-    return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
 
 
 def make_config(params: dict, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
@@ -237,6 +234,22 @@ class Server:
             raise self._err(rc)
         return buf[: n.value], int(sl.value), float(ms.value)
 
+    def attach_model(self, sid: int, model, max_log_n: float):
+        """Run learned per-ATV inference in every later close of stream sid."""
+        rc = lib().asse_server_attach_model(self._h, sid, model._h, float(max_log_n))
+        if rc != OK:
+            raise self._err(rc)
+
+    def estimates(self, sid: int, rows: int):
+        """(learned estimates [rows] float32 numpy array of the last polled
+        close of stream sid, number of Eq. 2 fallbacks)."""
+        out = np.zeros(rows, dtype=np.float32)
+        nfb = u32(0)
+        rc = lib().asse_server_estimates(self._h, sid, vp(out.ctypes.data), rows, HOST, ctypes.byref(nfb))
+        if rc != OK:
+            raise self._err(rc)
+        return out, int(nfb.value)
+
     def sync(self):
         rc = lib().asse_server_sync(self._h)
         if rc != OK:
@@ -285,6 +298,16 @@ class Pool:
     def set_stream(self, stream: int):
         self._stream = stream
         self._check(lib().asse_set_stream(self._h, vp(stream)))
+
+    def set_timing(self, on: bool = True):
+        """Record device events around the scan and restore of every close."""
+        self._check(lib().asse_set_timing(self._h, 1 if on else 0))
+
+    def close_timing(self):
+        """(scan ms, restore ms) of the last close recorded with timing on."""
+        ms = (ctypes.c_float * 2)()
+        self._check(lib().asse_close_timing(self._h, ms))
+        return float(ms[0]), float(ms[1])
 
     @property
     def launches(self) -> int:
@@ -371,10 +394,6 @@ class Pool:
         self._check(lib().asse_read_pool(self._h, vp(out.ctypes.data), HOST))
         return out.reshape(self.r, inf["E"], inf["words"])
 
-    def state(self) -> np.ndarray:
-        """Counter values [r][E][g] decoded from the packed pool."""
-        return unpack_pool(self.read_pool(), self._info, self.g)
-
     def snapshot(self) -> bytes:
         n = u64(0)
         self._check(lib().asse_snapshot(self._h, None, 0, ctypes.byref(n)))
@@ -405,6 +424,16 @@ class Pool:
                                                 vp(est.data_ptr()), vp(nfb.data_ptr())))
         return est, nfb, x
 
+    def candidate_features(self, aips):
+        """Candidate feature rows [n][FEAT] (torch bfloat16 on the device) of
+        the hosts aips (numpy or torch), between scan() and advance()."""
+        import torch
+        a = aips if _is_torch(aips) else torch.from_numpy(np.ascontiguousarray(aips, dtype=np.uint32).view(np.int32))
+        a = a.cuda().contiguous()
+        x = torch.empty((a.numel(), FEAT), dtype=torch.bfloat16, device="cuda")
+        self._check(lib().asse_candidate_features(self._h, vp(a.data_ptr()), a.numel(), vp(x.data_ptr())))
+        return x
+
     def features(self):
         """Feature rows [r*E][FEAT] (torch bfloat16 on the device) of every
         ATV, between scan() and advance()."""
@@ -412,6 +441,22 @@ class Pool:
         x = torch.empty((self.r * self._info["E"], FEAT), dtype=torch.bfloat16, device="cuda")
         self._check(lib().asse_features(self._h, vp(x.data_ptr())))
         return x
+
+
+def synth_candidates(cfg: dict, first: int, n: int, stream: int | None = None):
+    """Synthetic candidate states (include/asse_learn.h): (x [n][FEAT] bf16,
+    ln n [n] fp32, Eq. 4 estimate [n] fp32), torch tensors on the device."""
+    import torch
+    c = SynthCfg(int(cfg["k"]), int(cfg["g"]), int(cfg["r"]), int(cfg.get("n_max_log2", 20)),
+                 float(cfg.get("bg_max", 0.01)), 0, int(cfg["seed"]), int(cfg["bh_a"]), int(cfg["bh_b"]))
+    x = torch.empty((n, FEAT), dtype=torch.bfloat16, device="cuda")
+    ln = torch.empty(n, dtype=torch.float32, device="cuda")
+    e4 = torch.empty(n, dtype=torch.float32, device="cuda")
+    rc = lib().asse_synth_candidates(ctypes.byref(c), first, n, vp(x.data_ptr()), vp(ln.data_ptr()),
+                                     vp(e4.data_ptr()), vp(_current_stream() if stream is None else stream))
+    if rc != OK:
+        raise AsseError(rc, "asse_synth_candidates failed")
+    return x, ln, e4
 
 
 def synth_states(cfg: dict, first: int, n: int, stream: int | None = None):
@@ -477,6 +522,11 @@ class MLP:
             y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         self._check(lib().asse_mlp_forward(self._h, vp(x.data_ptr()), x.shape[0], vp(y.data_ptr())))
         return y
+
+    def set_loss(self, kind: str):
+        """'log_mse' (squared error of ln n, the default) or 'rel_mse'
+        (squared relative error of the estimate)."""
+        self._check(lib().asse_mlp_set_loss(self._h, {"log_mse": 0, "rel_mse": 1}[kind]))
 
     def check(self):
         """Synchronise; raises if a kernel of this model gave up a wait."""

@@ -1,6 +1,7 @@
 // Host side of the ASSE C ABI (include/asse.h): parameter validation, device
 // state, the slice lifecycle and the copies across the process/device
-// boundary.  All device work goes through the launchers of asse_kernels.cu.
+// boundary.  All device work goes through the kernel launchers declared in
+// asse_internal.h (asse_ingest.cu, asse_scan.cu, asse_restore.cu, asse_probe.cu).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -54,6 +55,9 @@ struct asse_pool {
     uint64_t report_host_cap = 0;
     int report_host_valid = 0;
     cudaEvent_t close_done = nullptr;  // recorded after those copies: a report waits for its close only
+    // asse_set_timing: events around the scan and the restore of each close
+    cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+    int timing = 0, timed = 0;
     SliceCtl *ctl = nullptr;  // device copy of the slice-dependent launch arguments
     uint32_t *stage[2] = {nullptr, nullptr};
     uint64_t stage_pairs = 0;
@@ -99,14 +103,6 @@ int cuda_fail(asse_pool *p, cudaError_t e, const char *what)
         if (e_ != cudaSuccess)                        \
             return cuda_fail((p), e_, #call);         \
     } while (0)
-
-uint32_t ceil_log2(uint32_t v)
-{
-    uint32_t b = 0;
-    while ((1u << b) < v)
-        b++;
-    return b;
-}
 
 uint64_t inverse_mod(uint64_t a, uint64_t m)
 {
@@ -155,7 +151,7 @@ int validate(const asse_config *c, std::string &why)
     if (c->key_table > ASSE_KEYS_OFF || c->pad != 0)
         return bad("key_table must be ASSE_KEYS_AUTO, ASSE_KEYS_ON or ASSE_KEYS_OFF, and pad 0");
     // the scan holds one ATV in a warp tile of at most 512 words
-    const uint32_t w = c->counter == ASSE_COUNTER_ACE ? (c->k == 1 ? 1 : ceil_log2(c->k + 1)) : ceil_log2(2 * c->k + 1);
+    const uint32_t w = packed_width(c->counter, c->k);
     if ((c->g + 32 / w - 1) / (32 / w) > 512)
         return bad("an ATV must fit in 512 words: need g <= 512 * floor(32 / w)");
     return ASSE_OK;
@@ -293,6 +289,9 @@ void free_all(asse_pool *p)
         cudaFreeHost(p->report_host);
     if (p->close_done)
         cudaEventDestroy(p->close_done);
+    for (cudaEvent_t ev : p->tev)
+        if (ev)
+            cudaEventDestroy(ev);
     for (int i = 0; i < 2; i++) {
         if (p->copied[i])
             cudaEventDestroy(p->copied[i]);
@@ -313,7 +312,7 @@ int pool_restore_view(asse_pool *p, RestoreView *v)
         return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
     p->report_host_valid = 0;
     v->P = p->P;
-    v->o = scan_out(p);
+    v->o = scan_out_w(p, p->sel);
     v->stream = p->stream;
     v->launches = &p->launches;
     return ASSE_OK;
@@ -321,14 +320,54 @@ int pool_restore_view(asse_pool *p, RestoreView *v)
 
 int pool_fail(asse_pool *p, int code, const std::string &msg) { return fail(p, code, msg); }
 
-int pool_enqueue_close(asse_pool *p, uint32_t kp)
+int pool_enqueue_close(asse_pool *p, uint32_t kp, bool timed)
 {
     if (int rc = reset_close_state(p))
         return rc;
+    if (timed)
+        CK(p, cudaEventRecord(p->tev[0], p->stream));
     CK(p, launch_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    if (timed)
+        CK(p, cudaEventRecord(p->tev[1], p->stream));
     CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
                          &p->launches, p->ctl));
+    if (timed)
+        CK(p, cudaEventRecord(p->tev[2], p->stream));
     return ASSE_OK;
+}
+
+int pool_enqueue_scan(asse_pool *p, uint32_t kp)
+{
+    if (int rc = reset_close_state(p))
+        return rc;
+    CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    return ASSE_OK;
+}
+
+int pool_enqueue_restore_refresh(asse_pool *p)
+{
+    CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
+                         &p->launches));
+    CK(p, launch_refresh(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
+    CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
+    return ASSE_OK;
+}
+
+FeatureView pool_feature_view_device(asse_pool *p, uint32_t kp)
+{
+    FeatureView v{};
+    v.P = p->P;
+    v.w = p->w;
+    v.pool = p->pool;
+    v.c0 = 0;
+    v.kp = kp;
+    v.ctl = p->ctl;
+    v.aat = p->aat;
+    v.cnt = p->cnt;
+    v.stream = p->stream;
+    v.launches = &p->launches;
+    v.sms = p->sms;
+    return v;
 }
 
 void pool_after_close(asse_pool *p, uint32_t kp)
@@ -367,8 +406,7 @@ PoolBuffers pool_buffers(asse_pool *p)
 // Device bytes asse_create allocates for cfg (the server's admission unit).
 uint64_t pool_device_bytes(const asse_config *cfg)
 {
-    const bool ace = cfg->counter == ASSE_COUNTER_ACE;
-    const uint32_t w = ace ? (cfg->k == 1 ? 1 : ceil_log2(cfg->k + 1)) : ceil_log2(2 * cfg->k + 1);
+    const uint32_t w = packed_width(cfg->counter, cfg->k);
     const uint32_t F = 32 / w;
     const uint64_t Wd = ((cfg->g + F - 1) / F + 7) / 8 * 8;
     const uint64_t n_atv = (uint64_t)cfg->r << (cfg->c + cfg->u);
@@ -394,6 +432,7 @@ int pool_feature_view(asse_pool *p, FeatureView *v)
     v->pool = p->pool;
     v->c0 = (uint32_t)(p->t % (2 * p->cfg.k));
     v->kp = p->scan_kp;
+    v->ctl = nullptr;
     v->aat = p->aat;
     v->cnt = p->cnt;
     v->stream = p->stream;
@@ -441,7 +480,7 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     p->stream = (cudaStream_t)stream;
     const uint32_t k = cfg->k;
     const bool ace = cfg->counter == ASSE_COUNTER_ACE;
-    p->w = ace ? (k == 1 ? 1 : ceil_log2(k + 1)) : ceil_log2(2 * k + 1);
+    p->w = packed_width(cfg->counter, k);
     p->F = 32 / p->w;
     p->words_used = (cfg->g + p->F - 1) / p->F;
     const uint32_t Wd = (p->words_used + 7) / 8 * 8;
@@ -677,9 +716,10 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (int rc = check_kp(p, kp))
         return rc;
-    if (int rc = pool_enqueue_close(p, kp))
+    if (int rc = pool_enqueue_close(p, kp, p->timing != 0))
         return rc;
     pool_after_close(p, kp);
+    p->timed = p->timing;
     CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
     CK(p, cudaMemcpyAsync(p->report_host, p->report, p->report_host_cap * sizeof(asse_superpoint),
                           cudaMemcpyDeviceToHost, p->stream));
@@ -740,6 +780,30 @@ int asse_close_slice_multi(asse_pool *p, const uint32_t *kps, uint32_t n_windows
                              p->stream, &p->launches, m + 1 == n_windows ? p->ctl : nullptr));
     pool_after_close(p, kps[0]);
     p->n_windows = n_windows;
+    return ASSE_OK;
+}
+
+int asse_set_timing(asse_pool *p, int on)
+{
+    if (!p)
+        return fail(nullptr, ASSE_EINVAL, "pool is NULL");
+    for (int i = 0; i < 3 && on; i++)
+        if (!p->tev[i])
+            CK(p, cudaEventCreate(&p->tev[i]));
+    p->timing = on ? 1 : 0;
+    p->timed = 0;
+    return ASSE_OK;
+}
+
+int asse_close_timing(asse_pool *p, float *ms)
+{
+    if (!p || !ms)
+        return fail(p, ASSE_EINVAL, "pool and ms must not be NULL");
+    if (!p->timed)
+        return fail(p, ASSE_ESTATE, "no close since asse_set_timing(pool, 1)");
+    CK(p, cudaEventSynchronize(p->tev[2]));
+    CK(p, cudaEventElapsedTime(&ms[0], p->tev[0], p->tev[1]));
+    CK(p, cudaEventElapsedTime(&ms[1], p->tev[1], p->tev[2]));
     return ASSE_OK;
 }
 

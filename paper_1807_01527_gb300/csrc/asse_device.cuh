@@ -172,8 +172,9 @@ __device__ __forceinline__ uint32_t u4get(const uint4 &v, int e)
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
-// Calls fn(std::integral_constant<int, w>) for the counter width w (1..8),
-// so that the field layout is a compile-time constant in every kernel.
+// Calls fn(std::integral_constant<int, w>) for the packed field width w (1..8
+// but not 7, which packed_width stores in 8 bits), so that the field layout
+// is a compile-time constant in every kernel.
 template <typename Fn>
 cudaError_t dispatch_w(uint32_t w, Fn &&fn)
 {
@@ -184,7 +185,6 @@ cudaError_t dispatch_w(uint32_t w, Fn &&fn)
     case 4: return fn(std::integral_constant<int, 4>());
     case 5: return fn(std::integral_constant<int, 5>());
     case 6: return fn(std::integral_constant<int, 6>());
-    case 7: return fn(std::integral_constant<int, 7>());
     case 8: return fn(std::integral_constant<int, 8>());
     default: return cudaErrorInvalidValue;
     }

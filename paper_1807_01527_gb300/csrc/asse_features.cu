@@ -18,12 +18,17 @@ constexpr int FEAT = ASSE_FEAT;
 constexpr int FEAT_WARPS = 8;
 
 // M: words per lane, the smallest of 4, 8, 16 that holds the ATV.
+// ctl non-null: C0 of the open slice comes from the device slice state (a
+// captured graph replays the launch slice after slice).
 template <int WB, int M>
 __global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, const uint32_t *pool, uint32_t c0,
-                                                                   uint32_t kp, const unsigned long long *aat, bf16 *x,
+                                                                   const SliceCtl *ctl, uint32_t kp,
+                                                                   const unsigned long long *aat, bf16 *x,
                                                                    uint32_t total_atv)
 {
     extern __shared__ uint32_t fsm[];
+    if (ctl)
+        c0 = ctl->c0;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint16_t *hist = reinterpret_cast<uint16_t *>(fsm + warp * HIST_WORDS);
     // load features of every (row, frame), then UP and mean P of every frame,
@@ -63,17 +68,10 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) features_kernel(Params P, con
 
 using namespace asse;
 
-extern "C" {
+namespace asse {
 
-int asse_features(asse_pool *pool, uint16_t *x_dev)
+cudaError_t launch_features(const FeatureView &v, uint16_t *x_dev)
 {
-    if (!pool || !x_dev)
-        return pool ? pool_fail(pool, ASSE_EINVAL, "x_dev is NULL") : ASSE_EINVAL;
-    FeatureView v;
-    if (int rc = pool_feature_view(pool, &v))
-        return rc;
-    if (v.kp > 64)
-        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
     const uint32_t total = v.P.r << v.P.E_log2;
     cudaError_t e = dispatch_w(v.w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
@@ -87,11 +85,28 @@ int asse_features(asse_pool *pool, uint16_t *x_dev)
         if (e2 != cudaSuccess)
             return e2;
         const unsigned grid = (unsigned)v.sms * 4;
-        kern<<<grid, FEAT_WARPS * 32, smem, v.stream>>>(v.P, v.pool, v.c0, v.kp, v.aat,
+        kern<<<grid, FEAT_WARPS * 32, smem, v.stream>>>(v.P, v.pool, v.c0, v.ctl, v.kp, v.aat,
                                                        reinterpret_cast<bf16 *>(x_dev), total);
         return cudaGetLastError();
     });
     *v.launches += 1;
+    return e;
+}
+
+}  // namespace asse
+
+extern "C" {
+
+int asse_features(asse_pool *pool, uint16_t *x_dev)
+{
+    if (!pool || !x_dev)
+        return pool ? pool_fail(pool, ASSE_EINVAL, "x_dev is NULL") : ASSE_EINVAL;
+    FeatureView v;
+    if (int rc = pool_feature_view(pool, &v))
+        return rc;
+    if (v.kp > 64)
+        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
+    const cudaError_t e = launch_features(v, x_dev);
     if (e != cudaSuccess)
         return pool_fail(pool, ASSE_ECUDA, std::string("features launch: ") + cudaGetErrorString(e));
     return ASSE_OK;

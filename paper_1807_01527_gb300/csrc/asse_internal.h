@@ -1,5 +1,6 @@
-// Internal declarations shared by the host API (asse_api.cu) and the
-// kernels (asse_kernels.cu).  Not part of the ABI.
+// Internal declarations shared by the host API (asse_api.cu) and the kernel
+// files (asse_ingest.cu, asse_scan.cu, asse_restore.cu, asse_probe.cu).  Not
+// part of the ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,6 +9,7 @@
 #include <string>
 
 #include "../../include/asse.h"
+#include "../../include/asse_learn.h"
 
 namespace asse {
 
@@ -35,6 +37,29 @@ struct Params {
     unsigned long long *keys;
     uint32_t klg;
 };
+
+// Bits of one counter field in the packed words: the counter's own width,
+// ceil(log2(2k+1)) for timestamps (values 0..2k, Sec. 3) or ceil(log2(k+1))
+// for aging counters (values 0..k), except that 7 becomes 8.  A word holds
+// floor(32/7) = floor(32/8) = 4 fields either way, so the byte-wide fields
+// cost no memory, and their top bit, never set by a 7-bit value, lets one
+// SWAR step test all four fields of a word (asse_swar.cuh).
+inline uint32_t packed_width(uint32_t counter, uint32_t k)
+{
+    uint32_t v = counter == ASSE_COUNTER_ACE ? k + 1 : 2 * k + 1, b = 0;
+    while ((1u << b) < v)
+        b++;
+    if (b == 0)
+        b = 1;
+    return b == 7 ? 8 : b;
+}
+
+// Byte-wide fields whose values stay below 128 (packed_width turned 7 into
+// 8): the scan tests them with the in-field guard bit.
+inline bool byte_guard(uint32_t w, uint32_t counter, uint32_t k)
+{
+    return w == 8 && (counter == ASSE_COUNTER_ACE ? k : 2 * k) < 128;
+}
 
 // Key table size for a pool of n_atv ATVs: 4 entries per ATV, 2^17 .. 2^22,
 // or none (0): with ASSE_KEYS_OFF, or with ASSE_KEYS_AUTO when the pool's
@@ -101,6 +126,8 @@ struct ScanGeom {
     uint32_t warps;       // warps per CTA that stream tiles
     uint32_t tile_offset; // byte offset of the tile buffers in dynamic shared memory
     uint32_t smem;        // dynamic shared memory bytes
+    uint32_t ilv;         // 1: interleaved chunks (lane p of an ATV owns its 16-byte chunks p, p + lpa, ...;
+                          //    the tile is apt whole ATVs back to back, one bulk copy); 0: lane segments
 };
 // nw windows: the count ranges of every window are kept in shared memory
 ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, uint32_t nw, size_t smem_limit);
@@ -196,7 +223,7 @@ struct ScanOut {
     Status *status;
 };
 
-// Kernel launchers (asse_kernels.cu).  Each returns the cudaError_t of its
+// Kernel launchers (asse_ingest.cu, asse_scan.cu, asse_restore.cu).  Each returns the cudaError_t of its
 // launch and adds the number of kernels it launched to *launches.
 // n pairs, or (n_dev != null) as many as *n_dev says at run time.
 cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uint32_t *pairs, uint64_t n,
@@ -253,6 +280,7 @@ struct FeatureView {
     uint32_t w;
     const uint32_t *pool;
     uint32_t c0, kp;
+    const SliceCtl *ctl;  // non-null: the kernel reads c0 from the device slice state (graph replays)
     const unsigned long long *aat;
     const uint16_t *cnt;  // |ATV|^{k'} of every ATV, from the same scan
     cudaStream_t stream;
@@ -260,13 +288,30 @@ struct FeatureView {
     int sms;
 };
 int pool_feature_view(asse_pool *p, FeatureView *v);
+// The view of a close enqueued by pool_enqueue_scan: no host bookkeeping
+// checks, C0 from the device slice state.
+FeatureView pool_feature_view_device(asse_pool *p, uint32_t kp);
+// Enqueue the feature rows of every ATV (asse_features.cu).
+cudaError_t launch_features(const FeatureView &v, uint16_t *x_dev);
+// Enqueue on v.stream the learned estimate of every ATV of the view: feature
+// rows into x_dev, the model, and est_dev = exp(model) inside the training
+// range, else Eq. 2 (asse_estimate_learned's rule); *nfb_dev counts the
+// fallbacks.  The model's parameters are only read (asse_learn.cu).
+int mlp_enqueue_learned(asse_mlp *m, const FeatureView &v, float max_log_n, uint16_t *x_dev, float *est_dev,
+                        uint32_t *nfb_dev, std::string *why);
 int pool_fail(asse_pool *p, int code, const std::string &msg);
 
 // Pieces of asse_close_slice / asse_ingest for the server (asse_serve.cu),
 // which captures them into CUDA graphs: enqueue the device work of a close
 // (no host bookkeeping), do the host bookkeeping of one close, and enqueue an
 // ingest whose pair count is read from device memory.
-int pool_enqueue_close(asse_pool *p, uint32_t kp);
+int pool_enqueue_close(asse_pool *p, uint32_t kp, bool timed = false);
+// The same close in three parts, for a close with learned inference between
+// the scan and the refresh (the refresh changes the state the features read):
+// the scan alone, then (after the caller's work) the restore, the refresh and
+// the opening of the next slice.
+int pool_enqueue_scan(asse_pool *p, uint32_t kp);
+int pool_enqueue_restore_refresh(asse_pool *p);
 void pool_after_close(asse_pool *p, uint32_t kp);
 int pool_enqueue_ingest(asse_pool *p, const uint32_t *pairs_dev, const unsigned long long *n_dev);
 struct PoolBuffers {

@@ -23,6 +23,7 @@
 #include "asse_device.cuh"
 #include "asse_features.cuh"
 #include "asse_mlp_tc.h"
+#include "asse_synth.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -42,9 +43,11 @@ constexpr size_t OFF_B3 = OFF_W3 + HID;
 constexpr size_t NPARAMS = OFF_B3 + 1;
 static_assert(NPARAMS == ASSE_MLP_NPARAMS, "parameter layout");
 
-// est[i] = exp(y[i]) where the model is inside its training range (the ATV
-// not saturated and 0 <= y <= max_log_n), else the linear-counting estimate
-// of Eq. 2 from the ATV's count (a saturated count g taken as g - 1/2).
+// est[i] = exp(max(y[i], 0)) where the ATV holds an active AT and the model
+// is inside its training range (y <= max_log_n, the log of the largest
+// cardinality it was trained on; a cardinality is at least 1), else the
+// linear-counting estimate of Eq. 2 from the ATV's count: 0 for an empty
+// ATV, and a saturated count g taken as g - 1/2.
 __global__ void learned_combine_kernel(const float *y, const uint16_t *cnt, uint32_t g, float max_log_n,
                                        uint64_t n, float *est, uint32_t *n_fallback)
 {
@@ -52,8 +55,8 @@ __global__ void learned_combine_kernel(const float *y, const uint16_t *cnt, uint
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float yi = y[i];
         const uint32_t c = cnt[i];
-        if (c < g && yi >= 0.0f && yi <= max_log_n) {
-            est[i] = expf(yi);
+        if (c > 0 && yi <= max_log_n) {
+            est[i] = expf(fmaxf(yi, 0.0f));
         } else {
             const double cc = c >= g ? (double)g - 0.5 : (double)c;
             est[i] = (float)(-(double)g * log(((double)g - cc) / (double)g));
@@ -66,29 +69,6 @@ __global__ void learned_combine_kernel(const float *y, const uint16_t *cnt, uint
 }
 
 // ---------------------------------------------------------------- synthetic states
-
-__device__ __forceinline__ uint64_t splitmix(uint64_t x)
-{
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-
-__device__ __forceinline__ double unit(uint64_t key, uint64_t i)
-{
-    return (double)(splitmix(key ^ splitmix(i)) >> 11) * (1.0 / 9007199254740992.0);
-}
-
-__device__ __forceinline__ uint32_t mix32(uint32_t x)
-{
-    x ^= x >> 16;
-    x *= 0x85EBCA6Bu;
-    x ^= x >> 13;
-    x *= 0xC2B2AE35u;
-    x ^= x >> 16;
-    return x;
-}
 
 struct SynthArgs {
     uint64_t seed;
@@ -359,14 +339,23 @@ __global__ void fill_kernel(float *y, uint64_t n, const float *value)
         y[i] = *value;
 }
 
-// dy = 2 (y - t) / n, loss += (y - t)^2 / n
-__global__ void loss_kernel(const float *y, const float *t, uint64_t n, float *dy, float *loss)
+// Squared error of the log: dy = 2 (y - t) / n, loss += (y - t)^2 / n.
+// Squared relative error of the estimate exp(y) against exp(t): with
+// e = exp(y - t), loss += (e - 1)^2 / n and dy = 2 (e - 1) e / n (y - t
+// clamped at 20 so that e stays finite).
+__global__ void loss_kernel(const float *y, const float *t, uint64_t n, int kind, float *dy, float *loss)
 {
     float acc = 0.0f;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float d = y[i] - t[i];
-        dy[i] = 2.0f * d / (float)n;
-        acc += d * d / (float)n;
+        if (kind == ASSE_LOSS_REL_MSE) {
+            const float e = expf(fminf(d, 20.0f));
+            dy[i] = 2.0f * (e - 1.0f) * e / (float)n;
+            acc += (e - 1.0f) * (e - 1.0f) / (float)n;
+        } else {
+            dy[i] = 2.0f * d / (float)n;
+            acc += d * d / (float)n;
+        }
     }
     acc += __shfl_xor_sync(FULL_MASK, acc, 16);
     acc += __shfl_xor_sync(FULL_MASK, acc, 8);
@@ -440,14 +429,6 @@ __global__ void to_bf16_kernel(const float *p, bf16 *w1b, bf16 *w2b)
     }
 }
 
-uint32_t ceil_log2_host(uint32_t v)
-{
-    uint32_t b = 0;
-    while ((1u << b) < v)
-        b++;
-    return b;
-}
-
 }  // namespace
 
 }  // namespace asse
@@ -464,6 +445,7 @@ struct asse_mlp {
     bf16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *y = nullptr, *dy = nullptr, *loss = nullptr;
     uint64_t steps = 0;
+    int loss_kind = ASSE_LOSS_LOG_MSE;
     uint64_t launches = 0;
     std::string err;
 };
@@ -533,7 +515,7 @@ int backward(asse_mlp *m, const bf16 *x, const float *t, uint64_t n, float *loss
     MCK(m, cudaMemsetAsync(G, 0, NPARAMS * sizeof(float), m->stream));
     MCK(m, cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
     const unsigned eb = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
-    loss_kernel<<<eb, 256, 0, m->stream>>>(m->y, t, n, m->dy, m->loss);
+    loss_kernel<<<eb, 256, 0, m->stream>>>(m->y, t, n, m->loss_kind, m->dy, m->loss);
     const unsigned rb = (unsigned)(n < 2048 ? n : 2048);
     out_grad_kernel<<<rb, HID, 0, m->stream>>>(m->dy, m->H2, m->params + OFF_W3, n, m->dZ2, G + OFF_W3, G + OFF_B2,
                                               G + OFF_B3);
@@ -556,13 +538,42 @@ int backward(asse_mlp *m, const bf16 *x, const float *t, uint64_t n, float *loss
     return ASSE_OK;
 }
 
-template <typename Fn>
-cudaError_t dispatch_w_host(uint32_t w, Fn &&fn)
+}  // namespace
+
+namespace asse {
+
+int mlp_enqueue_learned(asse_mlp *m, const FeatureView &v, float max_log_n, uint16_t *x_dev, float *est_dev,
+                        uint32_t *nfb_dev, std::string *why)
 {
-    return dispatch_w(w, fn);
+    cudaError_t e = launch_features(v, x_dev);
+    if (e != cudaSuccess) {
+        *why = std::string("features launch: ") + cudaGetErrorString(e);
+        return ASSE_ECUDA;
+    }
+    const uint64_t total = (uint64_t)v.P.r << v.P.E_log2;
+    // the model's outputs go to est_dev first, then are replaced in place
+    const int rc = launch_mlp_forward_tc(reinterpret_cast<const bf16 *>(x_dev), total, m->w1p, m->w2p, m->params,
+                                         est_dev, m->error, v.stream, v.launches, why);
+    if (rc != 0)
+        return rc == 1 ? ASSE_EINVAL : ASSE_ECUDA;
+    e = cudaMemsetAsync(nfb_dev, 0, sizeof(uint32_t), v.stream);
+    if (e == cudaSuccess) {
+        const unsigned grid = (unsigned)v.sms * 4;
+        learned_combine_kernel<<<grid, 256, 0, v.stream>>>(est_dev, v.cnt, v.P.g, max_log_n, total, est_dev,
+                                                           nfb_dev);
+        *v.launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        *why = std::string("learned combine: ") + cudaGetErrorString(e);
+        return ASSE_ECUDA;
+    }
+    return ASSE_OK;
 }
 
-}  // namespace
+}  // namespace asse
+
+using namespace asse;
 
 extern "C" {
 
@@ -578,21 +589,11 @@ int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, uint1
         return rc;
     if (mlp->stream != v.stream)
         return pool_fail(pool, ASSE_EINVAL, "the model and the pool must use the same stream");
-    if (int rc = asse_features(pool, x_dev))
-        return rc;
-    const uint64_t total = (uint64_t)v.P.r << v.P.E_log2;
-    // the model's outputs go to est_dev first, then are replaced in place
-    if (int rc = asse_mlp_forward(mlp, x_dev, total, est_dev))
-        return pool_fail(pool, rc, std::string("model: ") + mlp->err);
-    if (cudaMemsetAsync(n_fallback_dev, 0, sizeof(uint32_t), v.stream) != cudaSuccess)
-        return pool_fail(pool, ASSE_ECUDA, "memset of the fallback counter failed");
-    const unsigned grid = (unsigned)v.sms * 4;
-    learned_combine_kernel<<<grid, 256, 0, v.stream>>>(est_dev, v.cnt, v.P.g, max_log_n, total, est_dev,
-                                                       n_fallback_dev);
-    *v.launches += 1;
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return pool_fail(pool, ASSE_ECUDA, std::string("learned combine launch: ") + cudaGetErrorString(e));
+    if (v.kp > 64)
+        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
+    std::string why;
+    if (int rc = mlp_enqueue_learned(mlp, v, max_log_n, x_dev, est_dev, n_fallback_dev, &why))
+        return pool_fail(pool, rc, why);
     return ASSE_OK;
 }
 
@@ -615,7 +616,7 @@ int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uin
     P.blk_magic = ((1ull << 32) + P.blk - 1) / P.blk;
     P.bh_a = cfg->bh_a;
     P.bh_b = cfg->bh_b;
-    const uint32_t w = ceil_log2_host(2 * cfg->k + 1);
+    const uint32_t w = packed_width(ASSE_COUNTER_AT, cfg->k);
     const uint32_t Fw = 32 / w;
     P.Wd = ((cfg->g + Fw - 1) / Fw + 7) / 8 * 8;
     SynthArgs S{cfg->seed, cfg->n_max_log2, cfg->bg_max};
@@ -788,6 +789,16 @@ int asse_mlp_train_step(asse_mlp *m, const uint16_t *x_dev, const float *t_dev, 
     m->launches++;
     MCK(m, cudaGetLastError());
     MCK(m, launch_mlp_pack(m->params, m->w1p, m->w2p, m->stream, &m->launches));
+    return ASSE_OK;
+}
+
+int asse_mlp_set_loss(asse_mlp *m, int kind)
+{
+    if (!m)
+        return ASSE_EINVAL;
+    if (kind != ASSE_LOSS_LOG_MSE && kind != ASSE_LOSS_REL_MSE)
+        return mlp_fail(m, ASSE_EINVAL, "loss must be ASSE_LOSS_LOG_MSE or ASSE_LOSS_REL_MSE");
+    m->loss_kind = kind;
     return ASSE_OK;
 }
 

@@ -5,10 +5,12 @@
 // tiles of whole ATVs from global memory into shared memory with bulk async
 // copies (cp.async.bulk, completion on an mbarrier, two buffers per warp so the
 // next tile is in flight while this one is processed).  Inside a tile one lane
-// owns one ATV, or a 1/2, 1/4, 1/8 segment of a wide ATV; segments sit in
-// shared memory at a stride of an odd number of 16-byte units, so the lanes'
-// 128-bit reads never conflict.  All lanes walk the same word position at the
-// same time, so the per-position constants are warp-uniform.
+// owns one ATV, or a share of a wide ATV, in one of two layouts: a 1/2, 1/4,
+// 1/8 segment at a shared-memory stride of an odd number of 16-byte units, or
+// (interleaved) every lpa-th 16-byte chunk of an ATV stored back to back, when
+// the ATV length in chunks makes the lanes of a quarter warp hit distinct
+// banks; either way the lanes' 128-bit reads never conflict, and a tile of
+// whole, unpadded ATVs moves with one bulk copy.
 //
 // Activity test (Algorithm 1 on every field of a word at once): the active
 // values of a block form the cyclic window act-k'+1 .. act (mod 2k), i.e. at
@@ -38,17 +40,22 @@ namespace asse {
 
 namespace {
 
-constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_THREADS = 640;  // 20 warps: at most 102 registers a thread
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 
 // ---------------------------------------------------------------- scan kernel
 
 // NW: the most windows this instantiation counts (1, or MAX_WINDOWS for the
-// multi-window close, which runs W.n <= NW of them).
-template <int WB, bool FUSE, int NW>
+// multi-window close, which runs W.n <= NW of them).  BG: byte-wide fields
+// with values below 128, tested four at a time with the in-field guard bit
+// (one 16-byte range entry per word instead of two).
+// ILV: the interleaved tile layout (G.ilv), fixed at compile time so that
+// the per-word index arithmetic of the inner loop has no layout branch.
+template <int WB, bool FUSE, int NW, bool BG, bool ILV>
 __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_t *pool, const ScanWindows W,
                                                                const SliceCtl *ctl, uint32_t total_atv, ScanGeom G)
 {
+    static_assert(!BG || WB == 8, "the in-field guard needs byte-wide fields");
     const uint32_t c0 = ctl->c0;
     const Refresh R = ctl->R;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -58,6 +65,13 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     // Window m's table starts at m * n_cd.
     const uint32_t nw = NW == 1 ? 1u : W.n;
     const uint32_t n_cd = P.Wd + G.lpa;
+    const uint32_t nchunk = P.Wd / 4;
+    // index of word q's range entry in window m's table: skewed by segment
+    // (segments), or chunk-major per word of the chunk (interleaved), so that
+    // the lanes' reads of one step fall in distinct banks
+    auto didx = [&](uint32_t m, uint32_t q) {
+        return m * n_cd + (ILV ? (q & 3u) * nchunk + (q >> 2) : q + q / G.wseg);
+    };
     uint4 *cd_lo = reinterpret_cast<uint4 *>(smem);                          // [nw][Wd + lpa]
     uint4 *cd_hi = cd_lo + nw * n_cd;                                        // [nw][Wd + lpa]
     RangeDesc *rdesc = reinterpret_cast<RangeDesc *>(cd_hi + nw * n_cd);     // [Wd]
@@ -68,12 +82,20 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t e = threadIdx.x; e < nw * P.Wd; e += blockDim.x) {
         const uint32_t m = e / P.Wd, q = e - m * P.Wd;
-        const RangeDesc d = count_desc<WB>(P, q, c0, W.kp[m]);
-        const uint32_t x = m * n_cd + q + q / G.wseg;
-        cd_lo[x] = make_uint4(d.lo1e, d.hih1e, d.lo1o, d.hih1o);
-        cd_hi[x] = make_uint4(d.lo2e, d.hih2e, d.lo2o, d.hih2o);
-        if (FUSE && m == 0)
-            rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
+        const uint32_t x = didx(m, q);
+        if constexpr (BG) {
+            cd_lo[x] = count_desc_bytes(P, q, c0, W.kp[m]);
+            if (FUSE && m == 0) {
+                const uint4 r = refresh_desc_bytes(P, q, R.c0n);
+                rdesc[q] = RangeDesc{r.x, r.y, r.z, r.w, 0, 0, 0, 0};
+            }
+        } else {
+            const RangeDesc d = count_desc<WB>(P, q, c0, W.kp[m]);
+            cd_lo[x] = make_uint4(d.lo1e, d.hih1e, d.lo1o, d.hih1o);
+            cd_hi[x] = make_uint4(d.lo2e, d.hih2e, d.lo2o, d.hih2o);
+            if (FUSE && m == 0)
+                rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
+        }
     }
     if (warp < G.warps && lane == 0) {
         mbar_init(&mbar[2 * warp], 1);
@@ -84,8 +106,17 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
     if (warp >= G.warps)
         return;
 
-    const uint32_t a = lane / G.lpa, part = lane - a * G.lpa;  // this lane's ATV in the tile and segment
-    const uint32_t q_first = part * G.wseg;
+    const uint32_t a = lane / G.lpa, part = lane - a * G.lpa;  // this lane's ATV in the tile and share
+    const uint32_t q_first = ILV ? 4 * part : part * G.wseg;  // its first word
+    const uint32_t q_step = ILV ? 4 * G.lpa : 4;               // words between its chunks, in the ATV and in smem
+    const uint32_t lane_off = ILV ? a * P.Wd + 4 * part : lane * G.seg_stride;  // its first word in the tile
+    // word q of the tile's ATV a_ in shared memory
+    auto tile_word = [&](const uint32_t *tb, uint32_t a_, uint32_t q) {
+        if (ILV)
+            return tb[a_ * P.Wd + q];
+        const uint32_t pq = q / G.wseg;  // the segment holding word q
+        return tb[(a_ * G.lpa + pq) * G.seg_stride + (q - pq * G.wseg)];
+    };
     const uint32_t cols = P.cmask + 1;
     const uint32_t ntiles = (total_atv + G.apt - 1) / G.apt;
     uint32_t *my_mask = maskbuf + warp * P.mw;
@@ -97,7 +128,7 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
 
     // Segments of an odd number of 16-byte units need no padding: the tile
     // is then one contiguous stretch of the pool, fetched with one copy.
-    const bool whole = G.seg_stride == G.wseg;
+    const bool whole = ILV || G.seg_stride == G.wseg;
     auto issue = [&](uint32_t tile, int b) {
         const uint32_t atv0 = tile * G.apt;
         const uint32_t n_atv = min(G.apt, total_atv - atv0);
@@ -141,27 +172,41 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
         const uint32_t atv0 = tile * G.apt;
         const uint32_t n_atv = min(G.apt, total_atv - atv0);
         const bool mine = a < n_atv;
-        uint32_t *row = tile_buf(b) + lane * G.seg_stride;
+        uint32_t *row = tile_buf(b) + lane_off;
         uint32_t cnt[NW];
 #pragma unroll
         for (int m = 0; m < NW; m++)
             cnt[m] = 0;
         if (mine) {
 #pragma unroll 2
-            for (uint32_t i = 0; i < G.wseg; i += 4) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(row + i);
-                const uint32_t q = q_first + i;
+            for (uint32_t i = 0; i < G.wseg / 4; i++) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(row + i * q_step);
+                const uint32_t q = q_first + i * q_step;
 #pragma unroll
                 for (int m = 0; m < NW; m++) {
                     if (m < (int)nw) {
-                        const uint32_t xq = m * n_cd + q + part;
-                        cnt[m] += count_word<WB>(x.x, load_desc(cd_lo, cd_hi, xq)) +
-                                  count_word<WB>(x.y, load_desc(cd_lo, cd_hi, xq + 1)) +
-                                  count_word<WB>(x.z, load_desc(cd_lo, cd_hi, xq + 2)) +
-                                  count_word<WB>(x.w, load_desc(cd_lo, cd_hi, xq + 3));
+                        // the range entries of words q .. q+3: consecutive, or a chunk apart
+                        const uint32_t xq = didx(m, q), dx = ILV ? nchunk : 1u;
+                        if constexpr (BG) {
+                            // per-byte counts (at most 64 words per lane: no carry between bytes)
+                            cnt[m] += (in_ranges_bytes(x.x, cd_lo[xq]) >> 7) +
+                                      (in_ranges_bytes(x.y, cd_lo[xq + dx]) >> 7) +
+                                      (in_ranges_bytes(x.z, cd_lo[xq + 2 * dx]) >> 7) +
+                                      (in_ranges_bytes(x.w, cd_lo[xq + 3 * dx]) >> 7);
+                        } else {
+                            cnt[m] += count_word<WB>(x.x, load_desc(cd_lo, cd_hi, xq)) +
+                                      count_word<WB>(x.y, load_desc(cd_lo, cd_hi, xq + dx)) +
+                                      count_word<WB>(x.z, load_desc(cd_lo, cd_hi, xq + 2 * dx)) +
+                                      count_word<WB>(x.w, load_desc(cd_lo, cd_hi, xq + 3 * dx));
+                        }
                     }
                 }
             }
+        }
+        if constexpr (BG) {
+#pragma unroll
+            for (int m = 0; m < NW; m++)
+                cnt[m] = (cnt[m] * BYTE_ONES) >> 24;  // the four byte counts added
         }
         const uint32_t atv = atv0 + a;
         const bool head = mine && part == 0;
@@ -208,11 +253,10 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
                 __syncwarp();
                 {
                     constexpr uint32_t F = 32 / WB;
-                    const uint32_t *seg0 = tile_buf(b) + a_s * G.lpa * G.seg_stride;
                     for (uint32_t q = lane; q < P.Wd; q += 32) {
-                        const uint32_t pq = q / G.wseg;  // the segment holding word q
-                        const uint32_t word = seg0[pq * G.seg_stride + (q - pq * G.wseg)];
-                        const uint32_t am = field_bits<WB>(word, load_desc(cd_lo, cd_hi, m * n_cd + q + pq));
+                        const uint32_t word = tile_word(tile_buf(b), a_s, q);
+                        const uint32_t am = BG ? field_bits_bytes(word, cd_lo[didx(m, q)])
+                                               : field_bits<WB>(word, load_desc(cd_lo, cd_hi, didx(m, q)));
                         if (am) {
                             const uint32_t pos = q * F, off = pos & 31;
                             atomicOr(&my_mask[pos >> 5], am << off);
@@ -232,11 +276,18 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
         if (FUSE && !P.ace) {
             // Algorithm 2 for the next slice on the words of the two refreshed blocks
             for (uint32_t rr = 0; rr < R.n_ranges; rr++) {
-                const uint32_t lo = max(R.q_lo[rr], q_first), hi = min(R.q_hi[rr] + 1, q_first + G.wseg);
+                // segments: the lane's own words of the range; interleaved: the
+                // words of its chunks
+                const uint32_t lo = ILV ? R.q_lo[rr] : max(R.q_lo[rr], q_first);
+                const uint32_t hi = ILV ? R.q_hi[rr] + 1 : min(R.q_hi[rr] + 1, q_first + G.wseg);
                 if (mine) {
                     for (uint32_t q = lo; q < hi; q++) {
-                        const uint32_t w = row[q - q_first];
-                        const uint32_t nw = refresh_swar<WB>(P, w, rdesc[q]);
+                        if (ILV && ((q >> 2) & (G.lpa - 1)) != part)
+                            continue;
+                        const uint32_t w = tile_word(tile_buf(b), a, q);
+                        const RangeDesc &rd = rdesc[q];
+                        const uint32_t nw = BG ? refresh_bytes(P.k2, w, make_uint4(rd.lo1e, rd.hih1e, rd.lo1o, rd.hih1o))
+                                               : refresh_swar<WB>(P, w, rd);
                         if (nw != w)
                             pool[(size_t)atv * P.Wd + q] = nw;
                     }
@@ -245,12 +296,18 @@ __global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_
         }
         if (FUSE && P.ace) {
             // every aging counter loses one: decrement in place, store the segment back
-            if (mine) {
+            if (mine && !ILV) {
                 for (uint32_t i = 0; i < G.wseg; i++)
-                    row[i] = decay_swar<WB>(row[i]);
+                    row[i] = BG ? decay_bytes(row[i]) : decay_swar<WB>(row[i]);
                 fence_async_smem();
                 if (!whole)
                     bulk_store(pool + (size_t)atv * P.Wd + q_first, row, G.wseg * 4u);
+            }
+            if (ILV) {
+                uint32_t *tb = tile_buf(b);
+                for (uint32_t i = lane; i < n_atv * P.Wd; i += 32)
+                    tb[i] = BG ? decay_bytes(tb[i]) : decay_swar<WB>(tb[i]);
+                fence_async_smem();
             }
             if (whole) {
                 __syncwarp();
@@ -345,9 +402,19 @@ ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, uint32_t nw, size_t smem_limit)
         G.lpa *= 2;
     G.wseg = Wd / G.lpa;
     uint32_t units = G.wseg / 4;
-    if ((units & 1) == 0)
+    // Interleaved chunks where a segment would need padding and the ATV
+    // length S = Wd/4 chunks keeps the chunks the 8 lanes of a quarter warp
+    // read at once in distinct 16-byte bank groups: the quarter holds 8/lpa
+    // ATVs whose lanes read chunks a*S + p (+ i*lpa), distinct mod 8 when S is
+    // lpa times an odd number modulo 8 (any S with lpa = 8).
+    const uint32_t S = Wd / 4;
+    const bool ilv_ok = Wd % (4 * G.lpa) == 0 &&
+                        (G.lpa == 8 || (G.lpa == 4 && S % 8 == 4) || (G.lpa == 2 && S % 4 == 2) ||
+                         (G.lpa == 1 && S % 2 == 1));
+    G.ilv = (units & 1) == 0 && ilv_ok ? 1u : 0u;
+    if ((units & 1) == 0 && !G.ilv)
         units += 1;
-    G.seg_stride = units * 4;
+    G.seg_stride = G.ilv ? G.wseg : units * 4;
     G.apt = 32 / G.lpa;
     G.tile_words = 32 * G.seg_stride;
     const size_t fixed = (size_t)nw * (Wd + G.lpa) * 2 * sizeof(uint4) + (size_t)Wd * sizeof(RangeDesc);
@@ -372,13 +439,28 @@ cudaError_t launch_scan_nw(const Params &P, uint32_t w, uint32_t *pool, const Sc
     const uint32_t total = P.r << P.E_log2;
     const ScanGeom G = scan_geometry(P.Wd, P.mw, W.n, 200 * 1024);
     const uint32_t ntiles = (total + G.apt - 1) / G.apt;
+    const bool bg = byte_guard(w, P.ace ? ASSE_COUNTER_ACE : ASSE_COUNTER_AT, P.k);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        auto kern = scan_kernel<WB, true, NW>;
-        if constexpr (NW == 1) {
-            if (!fuse)
-                kern = scan_kernel<WB, false, 1>;
-        }
+        auto pick = [&](auto ilv) {
+            constexpr bool ILV = decltype(ilv)::value;
+            auto k = scan_kernel<WB, true, NW, false, ILV>;
+            if constexpr (NW == 1) {
+                if (!fuse)
+                    k = scan_kernel<WB, false, 1, false, ILV>;
+            }
+            if constexpr (WB == 8) {
+                if (bg) {
+                    k = scan_kernel<8, true, NW, true, ILV>;
+                    if constexpr (NW == 1) {
+                        if (!fuse)
+                            k = scan_kernel<8, false, 1, true, ILV>;
+                    }
+                }
+            }
+            return k;
+        };
+        auto kern = G.ilv ? pick(std::true_type()) : pick(std::false_type());
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem);
         if (e != cudaSuccess)
             return e;

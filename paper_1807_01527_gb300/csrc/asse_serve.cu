@@ -29,6 +29,10 @@ struct Slot {
     Status *status_host = nullptr;          // pinned
     asse_superpoint *report_host = nullptr; // pinned, rcap records
     uint64_t slice = 0;
+    // with a model attached: this close's learned estimates (device, r*E)
+    // and its count of Eq. 2 fallbacks (device, and its pinned copy)
+    float *est = nullptr;
+    uint32_t *nfb_dev = nullptr, *nfb_host = nullptr;
 };
 
 struct SStream {
@@ -43,6 +47,12 @@ struct SStream {
     cudaGraphExec_t ingest = nullptr;
     Slot ring[ASSE_SERVE_RING];
     uint32_t head = 0, count = 0;  // in-flight closes: ring[head] is the oldest
+    int last_polled = -1;          // slot of the close the last successful poll returned
+    // learned inference in the close graphs (asse_server_attach_model)
+    asse_mlp *mlp = nullptr;
+    float max_log_n = 0.0f;
+    uint16_t *x = nullptr;         // feature rows, [r*E][ASSE_FEAT] bf16, shared by the slots
+    uint64_t model_bytes = 0;
 };
 
 asse_config pool_cfg(const asse_config *cfg)
@@ -67,8 +77,13 @@ void release(SStream *st)
             cudaFreeHost(sl.status_host);
         if (sl.report_host)
             cudaFreeHost(sl.report_host);
+        cudaFree(sl.est);
+        cudaFree(sl.nfb_dev);
+        if (sl.nfb_host)
+            cudaFreeHost(sl.nfb_host);
         sl = Slot{};
     }
+    cudaFree(st->x);
     if (st->ingest)
         cudaGraphExecDestroy(st->ingest);
     cudaFree(st->staging);
@@ -94,6 +109,41 @@ cudaError_t capture(cudaStream_t s, cudaGraphExec_t *out, Fn &&enqueue, int *rc)
     if (g)
         cudaGraphDestroy(g);
     return e;
+}
+
+// Capture the close of one report slot: the fused close (scan with the
+// refresh, restore, next slice) or, with a model attached, the scan, the
+// learned inference of every ATV, then the restore, the refresh and the next
+// slice; then the copies of the status and the report (and the fallback
+// count) to the slot's pinned memory.
+cudaError_t capture_close(SStream *st, Slot &sl, const PoolBuffers &pb, int *rc)
+{
+    return capture(st->s, &sl.graph,
+                   [&]() {
+                       if (st->mlp) {
+                           if (int r = pool_enqueue_scan(st->pool, st->kp))
+                               return r;
+                           std::string why;
+                           const FeatureView v = pool_feature_view_device(st->pool, st->kp);
+                           if (int r = mlp_enqueue_learned(st->mlp, v, st->max_log_n, st->x, sl.est, sl.nfb_dev,
+                                                           &why))
+                               return pool_fail(st->pool, r, "learned inference: " + why);
+                           if (int r = pool_enqueue_restore_refresh(st->pool))
+                               return r;
+                           if (cudaMemcpyAsync(sl.nfb_host, sl.nfb_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                               st->s) != cudaSuccess)
+                               return (int)ASSE_ECUDA;
+                       } else if (int r = pool_enqueue_close(st->pool, st->kp)) {
+                           return r;
+                       }
+                       if (cudaMemcpyAsync(sl.status_host, pb.status, sizeof(Status), cudaMemcpyDeviceToHost,
+                                           st->s) != cudaSuccess ||
+                           cudaMemcpyAsync(sl.report_host, pb.report, st->rcap * sizeof(asse_superpoint),
+                                           cudaMemcpyDeviceToHost, st->s) != cudaSuccess)
+                           return (int)ASSE_ECUDA;
+                       return (int)ASSE_OK;
+                   },
+                   rc);
 }
 
 }  // namespace
@@ -210,18 +260,7 @@ int asse_server_open(asse_server *srv, const asse_config *cfg, uint32_t kp, uint
         if (e == cudaSuccess)
             e = cudaEventCreate(&sl.done);
         if (e == cudaSuccess)
-            e = capture(st->s, &sl.graph,
-                        [&]() {
-                            if (int r = pool_enqueue_close(st->pool, kp))
-                                return r;
-                            if (cudaMemcpyAsync(sl.status_host, pb.status, sizeof(Status), cudaMemcpyDeviceToHost,
-                                                st->s) != cudaSuccess ||
-                                cudaMemcpyAsync(sl.report_host, pb.report, st->rcap * sizeof(asse_superpoint),
-                                                cudaMemcpyDeviceToHost, st->s) != cudaSuccess)
-                                return ASSE_ECUDA;
-                            return ASSE_OK;
-                        },
-                        &rc);
+            e = capture_close(st, sl, pb, &rc);
     }
     if (e == cudaSuccess && rc == ASSE_OK)
         e = cudaStreamSynchronize(st->s);
@@ -301,6 +340,7 @@ int asse_server_poll(asse_server *srv, uint32_t id, asse_superpoint *out, uint64
     if (slice)
         *slice = sl.slice;
     const Status stt = *sl.status_host;
+    st->last_polled = (int)st->head;
     st->head = (st->head + 1) % ASSE_SERVE_RING;
     st->count--;
     if (stt.error)
@@ -342,6 +382,87 @@ int asse_server_close(asse_server *srv, uint32_t id)
         return srv ? sfail(srv, ASSE_EINVAL, "no such open stream") : ASSE_EINVAL;
     srv->in_use -= st->bytes;
     release(st);
+    return ASSE_OK;
+}
+
+int asse_server_attach_model(asse_server *srv, uint32_t id, asse_mlp *mlp, float max_log_n)
+{
+    SStream *st = get(srv, id);
+    if (!st || !mlp || !(max_log_n >= 0.0f))
+        return srv ? sfail(srv, ASSE_EINVAL, "no such open stream, NULL model or negative max_log_n") : ASSE_EINVAL;
+    if (st->kp > 64)
+        return sfail(srv, ASSE_EINVAL, "learned inference needs k' <= 64");
+    if (st->mlp)
+        return sfail(srv, ASSE_EINVAL, "a model is already attached to this stream");
+    if (st->count != 0)
+        return sfail(srv, ASSE_EAGAIN, "closes in flight: poll them first");
+    asse_pool_info info;
+    asse_info(st->pool, &info);
+    const uint64_t rows = (uint64_t)st->cfg.r * info.E;
+    const uint64_t bytes = rows * ASSE_FEAT * 2 + ASSE_SERVE_RING * (rows * sizeof(float) + sizeof(uint32_t));
+    if (srv->in_use + bytes > srv->budget)
+        return sfail(srv, ASSE_ENOMEM, "the model's buffers do not fit the device-memory budget now");
+    cudaError_t e = cudaStreamSynchronize(st->s);
+    if (e == cudaSuccess)
+        e = cudaMalloc((void **)&st->x, rows * ASSE_FEAT * 2);
+    for (Slot &sl : st->ring) {
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.est, rows * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.nfb_dev, sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&sl.nfb_host, sizeof(uint32_t));
+    }
+    st->mlp = mlp;
+    st->max_log_n = max_log_n;
+    const PoolBuffers pb = pool_buffers(st->pool);
+    int rc = ASSE_OK;
+    for (Slot &sl : st->ring) {
+        if (e != cudaSuccess || rc != ASSE_OK)
+            break;
+        if (sl.graph) {
+            cudaGraphExecDestroy(sl.graph);
+            sl.graph = nullptr;
+        }
+        e = capture_close(st, sl, pb, &rc);
+    }
+    if (e == cudaSuccess && rc == ASSE_OK)
+        e = cudaStreamSynchronize(st->s);
+    if (e != cudaSuccess || rc != ASSE_OK) {
+        // the stream is left unusable; close it to return its memory
+        const std::string why = e != cudaSuccess ? cudaGetErrorString(e) : asse_last_error(st->pool);
+        srv->in_use -= st->bytes;
+        release(st);
+        return sfail(srv, e == cudaErrorMemoryAllocation ? ASSE_ENOMEM : ASSE_ECUDA,
+                     "attach (the stream was closed): " + why);
+    }
+    st->model_bytes = bytes;
+    st->bytes += bytes;
+    srv->in_use += bytes;
+    return ASSE_OK;
+}
+
+int asse_server_estimates(asse_server *srv, uint32_t id, float *out, uint64_t cap, int where, uint32_t *n_fallback)
+{
+    SStream *st = get(srv, id);
+    if (!st || !out)
+        return srv ? sfail(srv, ASSE_EINVAL, "no such open stream or NULL argument") : ASSE_EINVAL;
+    if (!st->mlp || st->last_polled < 0)
+        return sfail(srv, ASSE_ESTATE, "no model attached or no close polled yet");
+    asse_pool_info info;
+    asse_info(st->pool, &info);
+    const uint64_t rows = (uint64_t)st->cfg.r * info.E;
+    if (cap < rows)
+        return sfail(srv, ASSE_ECAPACITY, "out holds fewer than r * E estimates");
+    const Slot &sl = st->ring[st->last_polled];
+    cudaError_t e = cudaMemcpyAsync(out, sl.est, rows * sizeof(float),
+                                    where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st->s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st->s);
+    if (e != cudaSuccess)
+        return sfail(srv, ASSE_ECUDA, std::string("estimates: ") + cudaGetErrorString(e));
+    if (n_fallback)
+        *n_fallback = *sl.nfb_host;
     return ASSE_OK;
 }
 

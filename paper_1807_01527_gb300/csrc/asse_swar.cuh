@@ -8,11 +8,13 @@
 // v >= lo and (hi | guard) - v keeps it iff v <= hi, with no borrow between
 // fields.  Per-position constants carry each field's own range, so words
 // that straddle two ACT blocks and the fields past g (empty ranges) need no
-// special case.
+// special case.  Byte-wide fields holding seven-bit values have the guard
+// bit inside the field and are tested all four at once (asse_bytes.h).
 #pragma once
 
 #include <cstdint>
 
+#include "asse_bytes.h"
 #include "asse_device.cuh"
 
 namespace asse {
@@ -194,6 +196,72 @@ __device__ __forceinline__ uint32_t decay_swar(uint32_t w)
     const uint32_t nz_e = ((xe | S::HE) - S::group_ones(0)) & S::HE;  // guard kept iff the field is >= 1
     const uint32_t nz_o = ((xo | S::HO) - S::group_ones(1)) & S::HO;
     return w - (nz_e >> WB) - ((nz_o >> WB) << WB);  // no borrow: each decremented field is >= 1
+}
+
+// ---------------------------------------------------------------------------
+// Byte-wide fields with values below 128 (asse_bytes.h): the range entries of
+// every word position, built like count_desc / refresh_desc but as four byte
+// lanes of one word each.
+
+// The count ranges of word position q (one ACT block per word is not
+// assumed: a word whose fields fall in two blocks gets per-byte ranges).
+__device__ __forceinline__ uint4 count_desc_bytes(const Params &P, uint32_t q, uint32_t c0, uint32_t kp)
+{
+    uint4 d = make_uint4(0, 0, 0, 0);
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t h = q * 4 + j;
+        uint32_t l1 = 127, h1 = 0, l2 = 127, h2 = 0;  // empty ranges
+        if (h < P.g) {
+            if (P.ace) {
+                l1 = P.k + 1 - kp;
+                h1 = P.k;
+            } else {
+                const uint32_t act = act_of(P, c0, act_block(P, h));
+                if (act + 1 >= kp) {
+                    l1 = act + 1 - kp;
+                    h1 = act;
+                } else {  // the window wraps past 0 to the top of 0..2k-1
+                    l1 = 0;
+                    h1 = act;
+                    l2 = act + P.k2 + 1 - kp;
+                    h2 = P.k2 - 1;
+                }
+            }
+        }
+        d.x |= l1 << (8 * j);
+        d.y |= (h1 | 0x80u) << (8 * j);
+        d.z |= l2 << (8 * j);
+        d.w |= (h2 | 0x80u) << (8 * j);
+    }
+    return d;
+}
+
+// The ranges Algorithm 2 clears in every byte of word position q when block 0
+// has ACT c0n.
+__device__ __forceinline__ uint4 refresh_desc_bytes(const Params &P, uint32_t q, uint32_t c0n)
+{
+    uint4 d = make_uint4(0, 0, 0, 0);
+    for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t h = q * 4 + j;
+        uint32_t l1 = 127, h1 = 0, l2 = 127, h2 = 0;
+        if (h < P.g && !P.ace) {
+            const uint32_t act = act_of(P, c0n, act_block(P, h));
+            if (act == 0) {
+                l1 = 0;
+                h1 = P.k;
+            } else if (act == P.k) {
+                l1 = P.k;
+                h1 = P.k2 - 1;
+                l2 = 0;
+                h2 = 0;
+            }
+        }
+        d.x |= l1 << (8 * j);
+        d.y |= (h1 | 0x80u) << (8 * j);
+        d.z |= l2 << (8 * j);
+        d.w |= (h2 | 0x80u) << (8 * j);
+    }
+    return d;
 }
 
 }  // namespace asse

@@ -247,6 +247,68 @@ def workload(name: str, seed: int = 1) -> Workload:
     raise KeyError(name)
 
 
+def _unit_sm(key: int, i) -> np.ndarray:
+    """The draw the training-state generator of the CUDA library uses:
+    SplitMix64(key ^ SplitMix64(i)), top 53 bits as a double in [0, 1)."""
+    i = np.asarray(i, dtype=np.uint64)
+    z = splitmix64(np.uint64(key) ^ splitmix64(i))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def training_state_draws(seed: int, index: int, k: int, g: int, n_max_log2: int, bg_max: float) -> dict:
+    """The random inputs of synthetic training state `index` (the library's
+    asse_synth_states draws the same numbers from the same counter-based
+    generator): the host's cardinality n, log-uniform in [1, 2^n_max_log2];
+    its split over the k slices by exponential shares, as the index ranges
+    [ends[s], ends[s+1]) of its distinct bips mix32(base + j); and the
+    background, which sets AT h in slice s with probability p (drawn in
+    [0, bg_max] per state) independently: bg[s][h]."""
+    key = int(splitmix64(np.uint64(seed & M64) ^ splitmix64(np.uint64((index + 0x51ED270B27) & M64))))
+    lnmax = n_max_log2 * 0.6931471805599453
+    card = max(1, int(math.floor(math.exp(float(_unit_sm(key, 1)) * lnmax))))
+    pbg = float(np.float32(float(_unit_sm(key, 2)) * float(np.float32(bg_max))))
+    w = [-math.log(float(_unit_sm(key, 16 + s)) + 1e-300) for s in range(k)]
+    tot = 0.0
+    for v in w:
+        tot += v
+    ends, cum = [0], 0.0
+    for s in range(k):
+        cum += w[s]
+        ends.append(card if s + 1 == k else int(math.floor(card * cum / tot)))
+    base = key >> 32
+    bips = [mix32((np.arange(ends[s], ends[s + 1], dtype=np.uint64) + np.uint64(base)).astype(np.uint32))
+            for s in range(k)]
+    idx = (np.arange(k, dtype=np.uint64)[:, None] << np.uint64(32)) | np.arange(g, dtype=np.uint64)[None, :]
+    bg = _unit_sm(key ^ 0xB5, idx) < pbg
+    return {"card": card, "pbg": pbg, "ends": ends, "bips": bips, "bg": bg}
+
+
+def candidate_state_draws(seed: int, index: int, k: int, g: int, r: int, n_max_log2: int, bg_max: float) -> dict:
+    """The random inputs of synthetic candidate state `index` (the library's
+    asse_synth_candidates draws the same numbers): the host's cardinality n
+    and its split over the k slices as in training_state_draws, and for each
+    of the r rows its own background probability p[i] in [0, bg_max] and the
+    ATs it sets, bg[i][s][h]."""
+    key = int(splitmix64(np.uint64(seed & M64) ^ splitmix64(np.uint64((index + 0x3C6EF372FE94F82B) & M64))))
+    lnmax = n_max_log2 * 0.6931471805599453
+    card = max(1, int(math.floor(math.exp(float(_unit_sm(key, 1)) * lnmax))))
+    p = [float(np.float32(float(_unit_sm(key, 4 + i)) * float(np.float32(bg_max)))) for i in range(r)]
+    w = [-math.log(float(_unit_sm(key, 16 + s)) + 1e-300) for s in range(k)]
+    tot = 0.0
+    for v in w:
+        tot += v
+    ends, cum = [0], 0.0
+    for s in range(k):
+        cum += w[s]
+        ends.append(card if s + 1 == k else int(math.floor(card * cum / tot)))
+    base = key >> 32
+    bips = [mix32((np.arange(ends[s], ends[s + 1], dtype=np.uint64) + np.uint64(base)).astype(np.uint32))
+            for s in range(k)]
+    idx = (np.arange(k, dtype=np.uint64)[:, None] << np.uint64(32)) | np.arange(g, dtype=np.uint64)[None, :]
+    bg = np.stack([_unit_sm(key ^ (0xB5 + 0x100 * (i + 1)), idx) < p[i] for i in range(r)])
+    return {"card": card, "p": p, "ends": ends, "bips": bips, "bg": bg}
+
+
 def random_pairs(seed: int, stream: int, n: int, n_hosts: int = 64, n_bips: int = 1 << 16) -> np.ndarray:
     """Small uniform test streams: n pairs over n_hosts aips and n_bips bips."""
     idx = np.arange(n, dtype=np.uint64)

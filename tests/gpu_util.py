@@ -18,12 +18,17 @@ def to_device(pairs):
     return torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.uint32).view(np.int32)).cuda()
 
 
-def mixed_pairs(seed: int, t: int, n: int, sizes, n_background: int = 200, bg_set: int = 6):
+def mixed_pairs(seed: int, t: int, n: int, sizes, n_background: int = 200, bg_set: int = 6, live=None):
     """n pairs of slice t: heavy hosts with bip sets of the given sizes (each
-    slice draws members at random), plus background hosts with small sets."""
+    slice draws members at random), plus background hosts with small sets.
+    live (one bool per heavy host) leaves the hosts that are not live out of
+    this slice."""
     sizes = np.asarray(sizes, dtype=np.int64)
     hosts = np.concatenate([sizes, np.full(n_background, bg_set, dtype=np.int64)])
-    weights = hosts.astype(np.float64) / hosts.sum()
+    weights = hosts.astype(np.float64)
+    if live is not None:
+        weights[: len(sizes)] *= np.asarray(live, dtype=np.float64)
+    weights /= weights.sum()
     cdf = np.cumsum(weights)
     idx = np.arange(n, dtype=np.uint64)
     u = synth.rand_unit(synth.key(seed, 0xE0, t), idx)
@@ -36,6 +41,30 @@ def mixed_pairs(seed: int, t: int, n: int, sizes, n_background: int = 200, bg_se
     out[:, 0] = aip
     out[:, 1] = bip
     return out
+
+
+def interval_pairs(seed: int, t: int, k: int, sizes, starts, lens, n_background: int = 3000):
+    """Slice t of a stream whose heavy hosts enter and leave the window: host
+    i is live in slices [starts[i], starts[i] + lens[i]) and then emits
+    ceil(4 sizes[i] / k) members of its bip set per slice, cycling through
+    the set, so its cardinality in a k-slice window grows over the first k/4
+    live slices and falls back to zero k slices after its last one.  Plus
+    n_background pairs of small background hosts.  Shuffled."""
+    parts = []
+    for i, (m, s0, ln) in enumerate(zip(sizes, starts, lens)):
+        if not (s0 <= t < s0 + ln):
+            continue
+        per = -(-4 * int(m) // k)
+        j = (np.arange(per, dtype=np.uint64) + np.uint64(t * per)) % np.uint64(m)
+        aip = synth.mix32(np.full(per, 0x7F000000 + i + seed * 7919, dtype=np.uint32))
+        with np.errstate(over="ignore"):
+            bip = synth.mix32((synth.mix32(aip).astype(np.uint64) + j).astype(np.uint32))
+        parts.append(np.stack([aip, bip], axis=1))
+    parts.append(mixed_pairs(seed, t, n_background, [], n_background=400, bg_set=5))
+    out = np.concatenate(parts).astype(np.uint32)
+    order = np.argsort(synth.rand_u64(synth.key(seed, 0xE2, t), np.arange(out.shape[0], dtype=np.uint64)),
+                       kind="stable")
+    return np.ascontiguousarray(out[order])
 
 
 def sp_rows(arr):
@@ -78,10 +107,25 @@ def check_close(pool, orc, kp, *, cap_ok=True):
     return res
 
 
+def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
+    """Packed pool words [r][E][words] -> counter values [r][E][g] (uint8):
+    field j of a word holds bits [j*w, j*w+w), AT h lives in word h // fields
+    (w and fields as asse_info reports them)."""
+    w, F = info["w"], info["fields"]
+    words = words.reshape(-1, info["E"], info["words"])
+    h = np.arange(g)
+    sel = words[:, :, h // F]
+    return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
+
+
+def state(pool) -> np.ndarray:
+    """Counter values [r][E][g] of a library pool, decoded from its packed words."""
+    return unpack_pool(pool.read_pool(), pool._info, pool.g)
+
+
 def assert_state_equal(pool, orc, what="", chunk=16384):
     """The pool's counters equal the oracle's, decoded a block of ATVs at a
     time (a full-size pool holds up to a billion counters)."""
-    from paper_1807_01527_gb300 import asse
     words = pool.read_pool()
     at = orc.at()
     info = dict(pool._info)
@@ -89,5 +133,5 @@ def assert_state_equal(pool, orc, what="", chunk=16384):
     for e in range(0, E, chunk):
         part = np.ascontiguousarray(words[:, e:e + chunk])
         info["E"] = part.shape[1]
-        np.testing.assert_array_equal(asse.unpack_pool(part, info, pool.g), at[:, e:e + chunk],
+        np.testing.assert_array_equal(unpack_pool(part, info, pool.g), at[:, e:e + chunk],
                                       err_msg="%s (ATVs %d..)" % (what, e))

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import check_close, compare_lists, mixed_pairs, to_device
+from gpu_util import check_close, compare_lists, interval_pairs, mixed_pairs, state, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -37,11 +37,11 @@ def test_tiny_b_every_slice(mods):
         pairs = w.pairs(t)
         pool.ingest(to_device(pairs))
         orc.ingest(pairs)
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after ingest t={t}")
         res = check_close(pool, orc, w.k)
         assert set(w.planted_aip.tolist()) <= {a for a, e, _n in res["report"]}
         orc.advance()
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
     pool.close()
 
 
@@ -57,7 +57,7 @@ def test_tiny_saturated_state_and_capacity(mods):
         pairs = w.pairs(t)
         pool.ingest(to_device(pairs))
         orc.ingest(pairs)
-        np.testing.assert_array_equal(pool.state(), orc.at())
+        np.testing.assert_array_equal(state(pool), orc.at())
         cnt = orc.counts(w.k)
         pool.close_slice(w.k)
         np.testing.assert_array_equal(pool.counts(), cnt)
@@ -68,17 +68,18 @@ def test_tiny_saturated_state_and_capacity(mods):
                 pool.report()
             assert ei.value.status == asse.ECAPACITY and ei.value.n_needed > pool.cap
         orc.advance()
-        np.testing.assert_array_equal(pool.state(), orc.at())
+        np.testing.assert_array_equal(state(pool), orc.at())
 
 
 # (k, g, r, c, u, s, counter): every counter width 1..8, r from 2 to 8,
 # frames 1..16, g not a multiple of the fields per word; ATVs of 8 to 88
 # words, so both scan tile layouts (padded lane segments, and whole tiles
-# when a segment is an odd number of 16-byte units) are covered
+# when a segment is an odd number of 16-byte units) are covered.  Every case
+# runs 2k+3 slices, past the point where C0 = t mod 2k wraps.
 CASES = [
     (1, 37, 4, 8, 0, 8, "at"), (2, 29, 4, 8, 0, 8, "at"), (3, 61, 3, 11, 1, 10, "at"),
     (5, 130, 5, 7, 1, 6, "at"), (10, 211, 4, 9, 2, 7, "at"), (20, 97, 8, 6, 2, 4, "at"),
-    (40, 257, 4, 8, 0, 8, "at"), (100, 333, 2, 16, 0, 16, "at"),
+    (40, 257, 4, 8, 0, 8, "at"), (100, 333, 3, 11, 1, 10, "at"), (6, 37, 2, 16, 0, 16, "at"),
     (1, 64, 4, 8, 0, 8, "ace"), (3, 50, 4, 9, 2, 7, "ace"), (5, 77, 5, 7, 1, 6, "ace"),
     (10, 128, 4, 8, 0, 8, "ace"), (20, 101, 3, 11, 1, 10, "ace"), (40, 300, 4, 8, 0, 8, "ace"),
     (100, 250, 4, 8, 0, 8, "ace"), (10, 570, 4, 8, 0, 8, "ace"),
@@ -86,7 +87,6 @@ CASES = [
     (1, 37, 4, 8, 0, 8, "aligned"), (4, 130, 4, 9, 2, 7, "aligned"), (10, 512, 4, 8, 0, 8, "aligned"),
     (12, 1024, 4, 8, 0, 8, "aligned"),
 ]
-
 
 @pytest.mark.parametrize("k,g,r,c,u,s,counter", CASES)
 def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
@@ -98,18 +98,62 @@ def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
     pool = asse.Pool(p, counter=counter, restore_cap=1 << 14, key_table="on" if (k + g) % 2 else "auto")
     orc = oracle.Oracle.from_params(p, mode=mode)
     heavy = [theta // 2, theta, 2 * theta, 3 * theta]
-    n_slices = min(2 * k + 3, 40) if k > 10 else 2 * k + 3
+    n_slices = 2 * k + 3
     rng = np.random.default_rng(k * 31 + g)
     for t in range(n_slices):
         n = int(rng.integers(0, 3000)) | 1 if t % 5 else int(rng.integers(0, 3))
         pairs = mixed_pairs(k + g, t, n, heavy)
         pool.ingest(to_device(pairs))
         orc.ingest(pairs)
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after ingest t={t}")
         kp = k if t % 3 else 1 + (t % k)
         check_close(pool, orc, kp)
         orc.advance()
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
+    pool.close()
+
+
+# The long workload's counters at small E: k = 60 (timestamps of 7 bits held
+# in byte-wide fields, four to a word, or 6-bit aging counters) with g = 1024
+# (an ATV of 256 words, scanned by eight lanes), and k = 30 (6-bit / 5-bit).
+EDGE_CASES = [(60, 1024, 4, 8, 1, 8, "at"), (60, 1024, 4, 8, 1, 8, "ace"), (60, 1024, 4, 8, 1, 8, "aligned"),
+              (30, 512, 4, 9, 2, 7, "at"), (30, 512, 4, 9, 2, 7, "ace")]
+
+
+@pytest.mark.parametrize("k,g,r,c,u,s,counter", EDGE_CASES)
+def test_window_edges_full_cycle(mods, k, g, r, c, u, s, counter):
+    """2k+3 slices (a full cycle of C0 and the wrap) of a stream whose heavy
+    hosts enter and leave the window at random slices: they become super
+    points, stay while the window holds enough of their bips, and vanish k
+    slices after their last packet (Sec. 3, Algorithms 1-2).  State after
+    every ingest and refresh, counts, loads, candidates and report against
+    the oracle, for k' = k and for shorter windows."""
+    asse, oracle, torch = mods
+    theta = g // 3
+    p = _params(k, g, r, c, u, s, theta, seed=k + 3 * g)
+    mode = {"at": 0, "ace": 1, "aligned": 2}[counter]
+    pool = asse.Pool(p, counter=counter, restore_cap=1 << 12)
+    orc = oracle.Oracle.from_params(p, mode=mode)
+    rng = np.random.default_rng(k * 7 + g)
+    n_heavy = 10
+    sizes = (theta * rng.uniform(0.5, 4.0, n_heavy)).astype(np.int64)
+    starts = rng.integers(0, k + 3, n_heavy)
+    lens = rng.integers(k // 4, k + 1, n_heavy)
+    reported, vanished = set(), set()
+    for t in range(2 * k + 3):
+        pairs = interval_pairs(k + g, t, k, sizes, starts, lens)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after ingest t={t}")
+        kp = k if t % 4 else max(1, k // (1 + t % 3))
+        res = check_close(pool, orc, kp)
+        now = {a for a, _e, _n in res["report"]}
+        if kp == k:
+            vanished |= reported - now
+        reported |= now
+        orc.advance()
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
+    assert len(reported) >= 3 and len(vanished) >= 3, (reported, vanished)   # hosts entered and left
     pool.close()
 
 
@@ -139,7 +183,7 @@ def test_aligned_stepwise_and_staggered_equivalence(mods):
         compare_lists(al.candidates(), orc.close_report(kp)["candidates"], p["theta"], "csip")
         al.advance()
         orc.advance()
-        np.testing.assert_array_equal(al.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(al), orc.at(), err_msg=f"after refresh t={t}")
     for pl in (al, st):
         pl.close()
 
@@ -176,26 +220,35 @@ def test_stepwise_equals_fused_and_estimate(mods):
             compare_lists(pl.candidates(), res["candidates"], p["theta"], "csip")
         orc.advance()
         np.testing.assert_array_equal(fused.read_pool(), step.read_pool())
-        np.testing.assert_array_equal(fused.state(), orc.at())
+        np.testing.assert_array_equal(state(fused), orc.at())
 
 
 def test_host_ingest_chunks_and_snapshot(mods):
-    """Host input copied in several double-buffered chunks equals device
-    input; a snapshot restored into a fresh pool continues identically."""
+    """Host input staged by the copy engines (pageable memory in ten
+    double-buffered chunks, and pinned memory) gives the oracle's state and
+    report, as device input does; a snapshot restored into a fresh pool
+    continues identically, also against the oracle."""
     asse, oracle, torch = mods
     p = _params(4, 128, 4, 10, 0, 8, 64, seed=3)
     a = asse.Pool(p, max_batch=1001)
     b = asse.Pool(p)
     c_pin = asse.Pool(p)
+    orc = oracle.Oracle.from_params(p)
     for t in range(5):
         pairs = mixed_pairs(3, t, 9999, [100, 200])
         a.ingest(pairs)                  # numpy: pageable host memory, staged in 10 chunks
         b.ingest(to_device(pairs))
-        c_pin.ingest(torch.from_numpy(pairs.view(np.int32)).pin_memory())   # pinned: read in place
-        np.testing.assert_array_equal(a.read_pool(), b.read_pool())
-        np.testing.assert_array_equal(c_pin.read_pool(), b.read_pool())
-        for pl in (a, b, c_pin):
+        c_pin.ingest(torch.from_numpy(pairs.view(np.int32)).pin_memory())   # pinned: staged in one chunk
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"staged ingest t={t}")
+        np.testing.assert_array_equal(state(c_pin), orc.at(), err_msg=f"pinned ingest t={t}")
+        np.testing.assert_array_equal(b.read_pool(), a.read_pool())
+        res = check_close(a, orc, 4)
+        for pl in (b, c_pin):
             pl.close_slice()
+            compare_lists(pl.report(), res["report"], orc.theta, "report t=%d" % t)
+        orc.advance()
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"after refresh t={t}")
     img = a.snapshot()
     c = asse.Pool(p)
     c.load(img)
@@ -203,10 +256,14 @@ def test_host_ingest_chunks_and_snapshot(mods):
     for t in range(5, 9):
         pairs = mixed_pairs(3, t, 5000, [100, 200])
         for pl in (a, c):
-            pl.ingest(to_device(pairs))
-            pl.close_slice()
+            pl.ingest(pairs)
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(c), orc.at(), err_msg=f"loaded pool t={t}")
+        res = check_close(c, orc, 4)
+        a.close_slice()
+        compare_lists(a.report(), res["report"], orc.theta, "report t=%d" % t)
+        orc.advance()
         np.testing.assert_array_equal(a.read_pool(), c.read_pool())
-        assert sorted(a.report()["aip"].tolist()) == sorted(c.report()["aip"].tolist())
     bad = asse.Pool(_params(5, 128, 4, 10, 0, 8, 64, seed=3))
     with pytest.raises(asse.AsseError) as ei:
         bad.load(img)
@@ -232,13 +289,13 @@ def test_key_table_repeats_and_slice_wrap(mods):
         for batch in (x, x, y):
             a.ingest(to_device(batch))
             orc.ingest(batch)
-        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after repeated batches t={t}")
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"after repeated batches t={t}")
         a.scan(4)
         a.ingest(to_device(x[::2]))
-        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after a batch past a scan t={t}")
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"after a batch past a scan t={t}")
         check_close(a, orc, 4)
         orc.advance()
-        np.testing.assert_array_equal(a.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"after refresh t={t}")
     img = bytearray(a.snapshot())
     off = 16 + ctypes.sizeof(asse.Config)
     assert int.from_bytes(img[off:off + 8], "little") == s0
@@ -253,7 +310,7 @@ def test_key_table_repeats_and_slice_wrap(mods):
             pl.ingest(to_device(x[::2]))
         orc.ingest(x)
         np.testing.assert_array_equal(b.read_pool(), a.read_pool(), err_msg=f"slice {t}")
-        np.testing.assert_array_equal(a.state(), orc.at())
+        np.testing.assert_array_equal(state(a), orc.at())
         check_close(a, orc, 4)
         b.close_slice(4)
         orc.advance()
@@ -293,7 +350,7 @@ def test_edge_cases(mods):
     one = mixed_pairs(9, 0, 1, [5])
     pool.ingest(to_device(one))                 # a single pair (tail path only)
     orc.ingest(one)
-    np.testing.assert_array_equal(pool.state(), orc.at())
+    np.testing.assert_array_equal(state(pool), orc.at())
     pool.ingest(one[:0])                        # empty batch
     with pytest.raises(asse.AsseError) as ei:
         pool.close_slice(4)                     # k' > k
@@ -324,16 +381,16 @@ def test_link_full_size_three_slices(mods):
         pairs = w.pairs(t)
         pool.ingest(to_device(pairs))
         orc.ingest(pairs)
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after ingest t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after ingest t={t}")
         check_close(pool, orc, w.k)
         orc.advance()
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
 
 
 @pytest.mark.parametrize("k,g,r,c,u,s,counter,n_win", [
     (6, 150, 4, 9, 2, 7, "at", 3), (10, 211, 4, 9, 2, 7, "at", 4), (5, 77, 5, 7, 1, 6, "ace", 4),
     (1, 64, 4, 8, 0, 8, "ace", 2), (20, 97, 8, 6, 2, 4, "at", 2), (40, 257, 4, 8, 0, 8, "at", 4),
-    (10, 570, 4, 8, 0, 8, "ace", 3)])
+    (10, 570, 4, 8, 0, 8, "ace", 3), (60, 1024, 4, 8, 1, 8, "at", 3)])
 def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
     """One pass over the pool for several windows k' <= k: every window's
     counts, loads, candidates and report equal the oracle's close for that
@@ -345,7 +402,7 @@ def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
     orc = oracle.Oracle.from_params(p, mode=1 if counter == "ace" else 0)
     heavy = [theta // 2, theta, 2 * theta, 3 * theta]
     rng = np.random.default_rng(k + 7 * g)
-    for t in range(min(2 * k + 3, 30)):
+    for t in range(2 * k + 3):
         n = int(rng.integers(1, 4000)) | 1
         pairs = mixed_pairs(k + g + 1, t, n, heavy)
         pool.ingest(to_device(pairs))
@@ -366,7 +423,7 @@ def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
         with pytest.raises(asse.AsseError):
             pool.select_window(len(kps))
         orc.advance()
-        np.testing.assert_array_equal(pool.state(), orc.at(), err_msg=f"after refresh t={t}")
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
     pool.close()
 
 

@@ -23,22 +23,37 @@ def _params(seed):
     return mlp.pack(q)
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_gradients_match_finite_differences(seed):
+@pytest.mark.parametrize("seed,loss_kind", [(1, "log_mse"), (2, "log_mse"), (3, "rel_mse"), (4, "rel_mse")])
+def test_gradients_match_finite_differences(seed, loss_kind):
     rng = np.random.default_rng(seed + 10)
     p = _params(seed)
     X = rng.normal(size=(12, mlp.FEAT))
     t = rng.normal(size=12)
-    loss, g, _y = mlp.loss_and_grads(p, X, t, rounding=False)
+    if loss_kind == "rel_mse":
+        # targets near the outputs: relative errors of order one, away from the clamp
+        t = mlp.forward(p, X, rounding=False)[0] + rng.normal(scale=0.7, size=12)
+    loss, g, _y = mlp.loss_and_grads(p, X, t, rounding=False, loss=loss_kind)
     idx = np.concatenate([rng.integers(0, mlp.NPARAMS, 60), [mlp.NPARAMS - 1]])
     eps = 1e-6
     for i in idx:
         e = np.zeros_like(p)
         e[i] = eps
-        lp = mlp.loss_and_grads(p + e, X, t, rounding=False)[0]
-        lm = mlp.loss_and_grads(p - e, X, t, rounding=False)[0]
+        lp = mlp.loss_and_grads(p + e, X, t, rounding=False, loss=loss_kind)[0]
+        lm = mlp.loss_and_grads(p - e, X, t, rounding=False, loss=loss_kind)[0]
         fd = (lp - lm) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
     # with rounding the loss moves by at most the BF16 perturbation of the activations
-    loss_r = mlp.loss_and_grads(p, X, t, rounding=True)[0]
-    assert abs(loss_r - loss) < 0.05 * max(1.0, loss)
+    loss_r = mlp.loss_and_grads(p, X, t, rounding=True, loss=loss_kind)[0]
+    assert abs(loss_r - loss) < (0.05 if loss_kind == "log_mse" else 0.15) * max(1.0, loss)
+
+
+def test_rel_mse_is_the_squared_relative_error():
+    """The relative loss is the mean squared relative error of exp(y)
+    against exp(t), computed here from the estimates themselves."""
+    rng = np.random.default_rng(7)
+    p = _params(5)
+    X = rng.normal(size=(20, mlp.FEAT))
+    t = rng.normal(size=20) + 3.0
+    loss, _g, y = mlp.loss_and_grads(p, X, t, rounding=False, loss="rel_mse")
+    n_hat, n_true = np.exp(y), np.exp(t)
+    assert abs(loss - np.mean(((n_hat - n_true) / n_true) ** 2)) <= 1e-12 * max(1.0, loss)

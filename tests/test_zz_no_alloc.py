@@ -27,7 +27,7 @@ def _same(got, want):
     assert [x[0] for x in g] == [x[0] for x in w]
     for a, b in zip(g, w):
         assert a[1] == b[1] and a[3] == b[3], (a, b)
-        assert a[2] == b[2] or (np.isinf(a[2]) and np.isinf(b[2])), (a, b)   # same kernel, same FP64 path
+        assert a[2] == b[2] or (np.isinf(a[2]) and np.isinf(b[2])), (a, b)   # the same restore kernel: bit-equal
 
 
 def test_static_restore_matches_pool_restore_twice_in_a_row():
@@ -62,6 +62,19 @@ def test_static_restore_matches_pool_restore_twice_in_a_row():
             checked += int(n[0])
         pool.advance()
     assert checked > 0
+    # after a close of two windows, the call restores the selected window
+    pool.ingest(to_device(w.pairs(4)))
+    pool.close_slice_multi([w.k, 2])
+    for m in (1, 0):
+        pool.select_window(m)
+        want_c = pool.candidates()
+        rc = L.asse_restore_static(pool._h, cap, vp(cand.data_ptr()), vp(rep.data_ptr()), cap,
+                                   vp(counters.data_ptr()))
+        assert rc == asse.OK, L.asse_last_error(pool._h)
+        torch.cuda.synchronize()
+        n = counters.cpu().numpy().view(np.uint64)
+        assert n[3] == 0 and n[0] == want_c.size
+        _same(cand.cpu().numpy().view(asse.SP_DTYPE)[: int(n[0])], want_c)
     # sizes beyond the fixed scratch are refused with a clear error
     too_many = asse.lib().asse_restore_static(pool._h, 65537, vp(cand.data_ptr()), vp(rep.data_ptr()), cap,
                                               vp(counters.data_ptr()))
