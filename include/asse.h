@@ -64,6 +64,18 @@ extern "C" {
  * of 2k blocks every slice.  Results equal the staggered pool's; the refresh
  * work comes in bursts of the whole pool every k slices. */
 #define ASSE_COUNTER_AT_ALIGNED 2
+/* Asynchronous timestamps (exactly ASSE_COUNTER_AT's counters, layout and
+ * results) plus, for every ATV, how many of its ATs each of the last 2k
+ * slices set (2k 16-bit counts, one per slice phase t mod 2k), kept by the
+ * ingest: a field that changes is set with a compare-and-swap, which returns
+ * its old value, and the counts of the old and the new slice are moved.  The
+ * close then counts |ATV|^{k'} from the k' latest counts instead of reading
+ * every AT (Sec. 3: the window's active ATs are those set in its slices), and
+ * reads AT words only for the super ATVs and the two blocks preserveAT
+ * checks.  A count is zeroed when its phase comes round again (every AT it
+ * counted has been cleared by then, Algorithm 2), so ATs cleared by the
+ * refresh need no update.  Costs 4k bytes per ATV. */
+#define ASSE_COUNTER_AT_HIST 3
 
 /* Flags of asse_superpoint. */
 #define ASSE_SP_SATURATED 1u /* NAT == g: Eq. 4 is +infinity */
@@ -84,7 +96,8 @@ extern "C" {
  *  A       mangling multiplier of f(aip) = A*aip mod (2^32+15), 2 <= A < 2^32.
  *  bh_a    BH multiplier (must be odd), bh_b BH offset:
  *          BH(bip) = (hi32(bh_a*bip + bh_b mod 2^64) * g) >> 32.
- *  counter ASSE_COUNTER_AT, ASSE_COUNTER_ACE or ASSE_COUNTER_AT_ALIGNED.
+ *  counter ASSE_COUNTER_AT, ASSE_COUNTER_ACE, ASSE_COUNTER_AT_ALIGNED or
+ *          ASSE_COUNTER_AT_HIST.
  *  restore_cap  column tuples held per frame at any join level of the
  *          restore; 0 selects 4096.  The candidate lists hold up to
  *          restore_cap * 2^u entries.

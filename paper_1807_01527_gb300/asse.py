@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libasse.so")
 
 OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE, EAGAIN = 0, 1, 2, 3, 4, 5, 6
 HOST, DEVICE = 0, 1
-COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED = 0, 1, 2
-COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED}
+COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED, COUNTER_AT_HIST = 0, 1, 2, 3
+COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED, "hist": COUNTER_AT_HIST}
 KEY_TABLE = {"auto": 0, "on": 1, "off": 2}
 SP_SATURATED, SP_REPORTED = 1, 2
 

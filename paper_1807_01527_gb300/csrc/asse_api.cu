@@ -123,8 +123,9 @@ int validate(const asse_config *c, std::string &why)
     auto bad = [&](const char *m) { why = m; return ASSE_EINVAL; };
     if (!c)
         return bad("cfg is NULL");
-    if (c->counter != ASSE_COUNTER_AT && c->counter != ASSE_COUNTER_ACE && c->counter != ASSE_COUNTER_AT_ALIGNED)
-        return bad("counter must be ASSE_COUNTER_AT, ASSE_COUNTER_ACE or ASSE_COUNTER_AT_ALIGNED");
+    if (c->counter != ASSE_COUNTER_AT && c->counter != ASSE_COUNTER_ACE && c->counter != ASSE_COUNTER_AT_ALIGNED &&
+        c->counter != ASSE_COUNTER_AT_HIST)
+        return bad("counter must be ASSE_COUNTER_AT, ASSE_COUNTER_ACE, ASSE_COUNTER_AT_ALIGNED or ASSE_COUNTER_AT_HIST");
     if (c->k < 1 || c->k > 127)
         return bad("k must be in [1, 127]");
     if (c->g < 2 * c->k || c->g > 4096)
@@ -275,6 +276,7 @@ void free_all(asse_pool *p)
     cudaFree(p->status);
     cudaFree(p->ctl);
     cudaFree(p->P.keys);
+    cudaFree(p->P.hist);
     cudaFree(p->stage[0]);
     cudaFree(p->stage[1]);
     cudaFree(p->q_aips);
@@ -326,6 +328,20 @@ int pool_enqueue_close(asse_pool *p, uint32_t kp, bool timed)
         return rc;
     if (timed)
         CK(p, cudaEventRecord(p->tev[0], p->stream));
+    if (p->P.hist) {
+        // counts from the slice counts; the refresh (with the zeroing of the
+        // next slice's counts) runs after the restore, then the next slice opens
+        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+        if (timed)
+            CK(p, cudaEventRecord(p->tev[1], p->stream));
+        CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
+                             &p->launches));
+        CK(p, launch_refresh(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
+        CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
+        if (timed)
+            CK(p, cudaEventRecord(p->tev[2], p->stream));
+        return ASSE_OK;
+    }
     CK(p, launch_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     if (timed)
         CK(p, cudaEventRecord(p->tev[1], p->stream));
@@ -340,7 +356,10 @@ int pool_enqueue_scan(asse_pool *p, uint32_t kp)
 {
     if (int rc = reset_close_state(p))
         return rc;
-    CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    if (p->P.hist)
+        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    else
+        CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     return ASSE_OK;
 }
 
@@ -418,7 +437,8 @@ uint64_t pool_device_bytes(const asse_config *cfg)
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
         cudaGetLastError();
     const uint32_t klg = key_table_log2(n_atv, n_atv * Wd * 4, (unsigned long long)l2, cfg->key_table);
-    return n_atv * Wd * 4 + n_atv * 2 + nseg * (8 + 4) + n_atv * 4 + n_atv * mw * 4 + nf * 2 * cap * sizeof(Tuple) +
+    const uint64_t hist = cfg->counter == ASSE_COUNTER_AT_HIST ? (uint64_t)2 * cfg->k * n_atv * 2 : 0;
+    return hist + n_atv * Wd * 4 + n_atv * 2 + nseg * (8 + 4) + n_atv * 4 + n_atv * mw * 4 + nf * 2 * cap * sizeof(Tuple) +
            2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8 +
            (klg ? sizeof(unsigned long long) << klg : 0);
 }
@@ -548,6 +568,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     P.klg = key_table_log2(n_atv, p->pool_words * 4, (unsigned long long)l2, cfg->key_table);
     if (P.klg)
         alloc((void **)&P.keys, sizeof(unsigned long long) << P.klg);
+    if (cfg->counter == ASSE_COUNTER_AT_HIST)
+        alloc((void **)&P.hist, (size_t)2 * k * n_atv * sizeof(uint16_t));
     alloc((void **)&p->stage[0], p->stage_pairs * 8);
     alloc((void **)&p->stage[1], p->stage_pairs * 8);
     if (e == cudaSuccess)
@@ -589,6 +611,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
         e = cudaMemsetAsync(p->status, 0, sizeof(Status), p->stream);
     if (e == cudaSuccess && P.keys)
         e = cudaMemsetAsync(P.keys, 0xff, sizeof(unsigned long long) << P.klg, p->stream);
+    if (e == cudaSuccess && P.hist)
+        e = cudaMemsetAsync(P.hist, 0, (size_t)2 * k * n_atv * sizeof(uint16_t), p->stream);
     const SliceCtl ctl0 = slice_ctl(P, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, p->stream);
@@ -671,9 +695,8 @@ int asse_scan(asse_pool *p, uint32_t kp)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (int rc = check_kp(p, kp))
         return rc;
-    if (int rc = reset_close_state(p))
+    if (int rc = pool_enqueue_scan(p, kp))
         return rc;
-    CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     p->n_windows = 1;
     p->sel = 0;
     p->report_host_valid = 0;
@@ -774,10 +797,22 @@ int asse_close_slice_multi(asse_pool *p, const uint32_t *kps, uint32_t n_windows
         W.o[m] = scan_out_w(p, m);
         CK(p, launch_reset(W.o[m].aat, W.o[m].sa_n, p->cfg.r * p->P.nf, W.o[m].status, p->stream, &p->launches));
     }
-    CK(p, launch_scan_windows(p->P, p->w, p->pool, W, p->ctl, p->sms, p->stream, &p->launches));
-    for (uint32_t m = 0; m < n_windows; m++)
-        CK(p, launch_restore(p->P, W.o[m], p->scratch, p->cap, list_w(p, m, false), list_w(p, m, true), p->out_cap,
-                             p->stream, &p->launches, m + 1 == n_windows ? p->ctl : nullptr));
+    if (p->P.hist) {
+        // one count pass per window over the slice counts, then the restores,
+        // the refresh (with the zeroing of the next slice's counts) and the next slice
+        for (uint32_t m = 0; m < n_windows; m++)
+            CK(p, launch_hist_scan(p->P, p->w, p->pool, kps[m], p->ctl, W.o[m], p->sms, p->stream, &p->launches));
+        for (uint32_t m = 0; m < n_windows; m++)
+            CK(p, launch_restore(p->P, W.o[m], p->scratch, p->cap, list_w(p, m, false), list_w(p, m, true),
+                                 p->out_cap, p->stream, &p->launches));
+        CK(p, launch_refresh(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
+        CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
+    } else {
+        CK(p, launch_scan_windows(p->P, p->w, p->pool, W, p->ctl, p->sms, p->stream, &p->launches));
+        for (uint32_t m = 0; m < n_windows; m++)
+            CK(p, launch_restore(p->P, W.o[m], p->scratch, p->cap, list_w(p, m, false), list_w(p, m, true),
+                                 p->out_cap, p->stream, &p->launches, m + 1 == n_windows ? p->ctl : nullptr));
+    }
     pool_after_close(p, kps[0]);
     p->n_windows = n_windows;
     return ASSE_OK;
@@ -979,6 +1014,9 @@ int asse_load(asse_pool *p, const void *src, uint64_t n)
     // the key table describes the replaced state
     if (p->P.keys)
         CK(p, cudaMemsetAsync(p->P.keys, 0xff, sizeof(unsigned long long) << p->P.klg, p->stream));
+    // slice counts of a histogram pool, counted again from the loaded words
+    if (p->P.hist)
+        CK(p, launch_hist_rebuild(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
     CK(p, cudaStreamSynchronize(p->stream));
     p->t = h.slice;
     p->scanned = p->restored = p->refreshed = 0;

@@ -1,0 +1,168 @@
+// The close of a pool with slice counts (ASSE_COUNTER_AT_HIST).
+//
+// The ingest keeps, for every ATV, how many of its ATs each slice phase
+// (t mod 2k) set last (asse_ingest.cu).  An AT is active in the window of the
+// latest k' slices iff it was set in one of them (Sec. 3), so |ATV|^{k'} is
+// the sum of the counts of the k' latest phases: one 2-byte read per ATV and
+// phase, coalesced across the ATVs (the counts are phase-major), instead of
+// the whole ATV.  The row-frame loads and the super-ATV lists follow as in
+// the full scan; only a super ATV's words are read, to build its g-bit active
+// mask for Algorithm 5.  The refresh of the two checked blocks (Algorithm 2)
+// runs in the standalone refresh kernel, which also zeroes the counts of the
+// opening slice's phase.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "asse_device.cuh"
+#include "asse_swar.cuh"
+
+namespace asse {
+
+namespace {
+
+constexpr int HIST_THREADS = 256;
+constexpr int HIST_WARPS = HIST_THREADS / 32;
+
+template <int WB>
+__global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, const uint32_t *pool, uint32_t kp,
+                                                                 const SliceCtl *ctl, ScanOut o, uint32_t total_atv)
+{
+    constexpr uint32_t F = 32 / WB;
+    extern __shared__ __align__(16) uint8_t hsm[];
+    RangeDesc *desc = reinterpret_cast<RangeDesc *>(hsm);                  // [Wd]
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(desc + P.Wd);         // [warps][mw]
+    const uint32_t c0 = ctl->c0;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x)
+        desc[q] = count_desc<WB>(P, q, c0, kp);
+    __syncthreads();
+    uint32_t *my_mask = maskbuf + warp * P.mw;
+    const uint32_t cols = P.cmask + 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < total_atv; base += stride) {
+        const uint64_t atv = base + lane;
+        const bool mine = atv < total_atv;
+        uint32_t c = 0;
+        if (mine) {
+            // phases c0, c0-1, ..., c0-k'+1 (mod 2k): the slices of the window
+            uint32_t ph = c0;
+            for (uint32_t a = 0; a < kp; a++) {
+                c += P.hist[(uint64_t)ph * total_atv + atv];
+                ph = ph == 0 ? P.k2 - 1 : ph - 1;
+            }
+            o.cnt[atv] = (uint16_t)c;
+        }
+        const uint32_t sg = mine ? (uint32_t)(atv >> P.c) : 0xffffffffu;  // row * 2^u + frame
+        const unsigned grp = __match_any_sync(FULL_MASK, sg);
+        {
+            const uint32_t s = __reduce_add_sync(grp, mine ? c : 0u);
+            if (mine && (uint32_t)(__ffs(grp) - 1) == lane && s)
+                atomicAdd(&o.aat[sg], (unsigned long long)s);
+        }
+        const bool sup = mine && c >= P.T;
+        uint32_t slot = 0;
+        if (sup) {
+            slot = atomicAdd(&o.sa_n[sg], 1u);
+            o.sa_x[(size_t)sg * cols + slot] = (uint32_t)atv & P.cmask;
+        }
+        unsigned sbits = __ballot_sync(FULL_MASK, sup);
+        while (sbits) {
+            // the g-bit active mask of one super ATV from its words
+            const uint32_t hl = __ffs(sbits) - 1;
+            sbits &= sbits - 1;
+            const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
+            const uint64_t atv_a = base + hl;
+            const uint32_t sg_a = (uint32_t)(atv_a >> P.c);
+            for (uint32_t k = lane; k < P.mw; k += 32)
+                my_mask[k] = 0;
+            __syncwarp();
+            for (uint32_t q = lane; q < P.Wd; q += 32) {
+                const uint32_t word = pool[atv_a * P.Wd + q];
+                const uint32_t am = field_bits<WB>(word, desc[q]);
+                if (am) {
+                    const uint32_t pos = q * F, off = pos & 31;
+                    atomicOr(&my_mask[pos >> 5], am << off);
+                    if (off + F > 32 && (am >> (32 - off)))
+                        atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
+                }
+            }
+            __syncwarp();
+            uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
+            for (uint32_t k = lane; k < P.mw; k += 32)
+                dst[k] = my_mask[k];
+            __syncwarp();
+        }
+    }
+}
+
+// The slice counts of a pool counted from its words (after asse_load): every
+// AT set d < k slices ago, d = (ACT - value) mod 2k, adds one to the count of
+// phase t - d.  Counts of older phases stay zero (no window reads them).
+template <int WB>
+__global__ void __launch_bounds__(HIST_THREADS) hist_rebuild_kernel(Params P, const uint32_t *pool, const SliceCtl *ctl,
+                                                                    uint32_t total_atv)
+{
+    constexpr uint32_t F = 32 / WB;
+    constexpr uint32_t FM = (1u << WB) - 1;
+    const uint32_t c0 = ctl->c0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t atv = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; atv < total_atv; atv += stride) {
+        for (uint32_t q = 0; q < P.Wd; q++) {
+            const uint32_t word = pool[atv * P.Wd + q];
+            for (uint32_t j = 0; j < F; j++) {
+                const uint32_t h = q * F + j;
+                const uint32_t v = (word >> (j * WB)) & FM;
+                if (h >= P.g || v >= P.k2)
+                    continue;
+                uint32_t age = act_of(P, c0, act_block(P, h)) + P.k2 - v;
+                age = age >= P.k2 ? age - P.k2 : age;
+                if (age < P.k) {
+                    const uint32_t ph = c0 >= age ? c0 - age : c0 + P.k2 - age;
+                    hist_add(P.hist, (uint64_t)ph * total_atv + atv, 1);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_hist_scan(const Params &P, uint32_t w, const uint32_t *pool, uint32_t kp, const SliceCtl *ctl,
+                             const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches)
+{
+    const uint32_t total = P.r << P.E_log2;
+    const size_t smem = (size_t)P.Wd * sizeof(RangeDesc) + (size_t)HIST_WARPS * P.mw * sizeof(uint32_t);
+    *launches += 1;
+    return dispatch_w(w, [&](auto wb) {
+        constexpr int WB = decltype(wb)::value;
+        cudaError_t e = cudaFuncSetAttribute(hist_scan_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        const uint64_t want = (total + HIST_THREADS - 1) / HIST_THREADS;
+        const uint64_t full = (uint64_t)sms * resident_blocks(hist_scan_kernel<WB>, HIST_THREADS, smem);
+        hist_scan_kernel<WB><<<(unsigned)(want < full ? want : full), HIST_THREADS, smem, s>>>(P, pool, kp, ctl, o,
+                                                                                             total);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_hist_rebuild(const Params &P, uint32_t w, const uint32_t *pool, const SliceCtl *ctl, int sms,
+                                cudaStream_t s, uint64_t *launches)
+{
+    const uint32_t total = P.r << P.E_log2;
+    cudaError_t e = cudaMemsetAsync(P.hist, 0, (size_t)P.k2 * total * sizeof(uint16_t), s);
+    if (e != cudaSuccess)
+        return e;
+    *launches += 1;
+    return dispatch_w(w, [&](auto wb) {
+        constexpr int WB = decltype(wb)::value;
+        const uint64_t want = (total + HIST_THREADS - 1) / HIST_THREADS;
+        const uint64_t full = (uint64_t)sms * resident_blocks(hist_rebuild_kernel<WB>, HIST_THREADS, 0);
+        hist_rebuild_kernel<WB><<<(unsigned)(want < full ? want : full), HIST_THREADS, 0, s>>>(P, pool, ctl, total);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace asse

@@ -107,10 +107,41 @@ __device__ __forceinline__ bool claim_key(const Params &P, uint32_t gen, uint32_
     return atomicExch(slot, want) != want;
 }
 
+// SetAT with slice counts (ASSE_COUNTER_AT_HIST): the field is set with a
+// compare-and-swap, which tells its old value f; if this lane changed it,
+// the count of the open slice's phase gains one and, if f was set less than
+// k slices ago, the count of f's slice loses one (a count older than that
+// is outside every window and is zeroed before its phase comes round again).
+__device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, uint32_t old, uint32_t sh, uint32_t val,
+                                               uint32_t fm, uint32_t c0, uint32_t atv)
+{
+    uint32_t f;
+    for (;;) {
+        f = (old >> sh) & fm;
+        if (f == val)
+            return;  // already the slice's value: nothing changes
+        const uint32_t nw = (old & ~(fm << sh)) | (val << sh);
+        const uint32_t prev = atomicCAS(addr, old, nw);
+        if (prev == old)
+            break;
+        old = prev;
+    }
+    const uint64_t n_atv = (uint64_t)P.r << P.E_log2;
+    hist_add(P.hist, (uint64_t)c0 * n_atv + atv, 1);
+    if (f != P.k2) {
+        uint32_t age = val + P.k2 - f;  // (ACT now - ACT then) mod 2k: slices since f was set
+        age = age >= P.k2 ? age - P.k2 : age;
+        if (age < P.k) {
+            const uint32_t ph = c0 >= age ? c0 - age : c0 + P.k2 - age;
+            hist_add(P.hist, (uint64_t)ph * n_atv + atv, -1);
+        }
+    }
+}
+
 // Algorithm 3 for one key (aip, h = BH(bip)) of this lane, if ok: f(aip), the
 // r column windows, the ACT of AT h, the r word loads together, then the
-// field sets.
-template <int WB, int R>
+// field sets (with the slice counts when HIST).
+template <int WB, int R, bool HIST = false>
 __device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_t c0, int r, uint32_t aip, uint32_t h,
                                         bool ok)
 {
@@ -136,16 +167,21 @@ __device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_
         if (i < r)
             o[i] = *a[i];
 #pragma unroll
-    for (int i = 0; i < RM; i++)
-        if (i < r)
-            set_field(a[i], o[i], sh, val, FM);
+    for (int i = 0; i < RM; i++) {
+        if (i < r) {
+            if constexpr (HIST)
+                set_field_hist(P, a[i], o[i], sh, val, FM, c0, (uint32_t)((a[i] - pool) / P.Wd));
+            else
+                set_field(a[i], o[i], sh, val, FM);
+        }
+    }
 }
 
 // Keys new to the block (one per lane, if ok) are claimed in the key table;
 // the ones new to the slice join the warp's second queue, and every 32 of
 // those run Algorithm 3 with all lanes busy.  Without a key table, Algorithm
 // 3 runs on them directly.
-template <int WB, int R>
+template <int WB, int R, bool HIST>
 __device__ __forceinline__ void claim_and_set(const Params &P, uint32_t *pool, uint32_t c0, uint32_t gen, int r,
                                               uint2 e, bool ok, uint2 *q2, uint32_t &q2n, unsigned lt)
 {
@@ -164,10 +200,10 @@ __device__ __forceinline__ void claim_and_set(const Params &P, uint32_t *pool, u
             __syncwarp();
         }
     }
-    set_key<WB, R>(P, pool, c0, r, e.x, e.y, run);
+    set_key<WB, R, HIST>(P, pool, c0, r, e.x, e.y, run);
 }
 
-template <int WB, int R>
+template <int WB, int R, bool HIST>
 __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     ingest_kernel(Params P, uint32_t *pool, const uint32_t *__restrict__ pairs_raw, uint64_t n_arg,
                   const unsigned long long *n_dev, const SliceCtl *ctl)
@@ -222,23 +258,23 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
             qn -= 32;
             const uint2 e = queue[qn + lane];
             __syncwarp();
-            claim_and_set<WB, R>(P, pool, c0, gen, r, e, true, q2, q2n, lt);
+            claim_and_set<WB, R, HIST>(P, pool, c0, gen, r, e, true, q2, q2n, lt);
         }
     }
     __syncwarp();
     if (qn > 0) {
         const bool ok = lane < qn;
-        claim_and_set<WB, R>(P, pool, c0, gen, r, ok ? queue[lane] : make_uint2(0, 0), ok, q2, q2n, lt);
+        claim_and_set<WB, R, HIST>(P, pool, c0, gen, r, ok ? queue[lane] : make_uint2(0, 0), ok, q2, q2n, lt);
     }
     __syncwarp();
     if (q2n > 0) {
         const bool ok = lane < q2n;
         const uint2 f = ok ? q2[lane] : make_uint2(0, 0);
-        set_key<WB, R>(P, pool, c0, r, f.x, f.y, ok);
+        set_key<WB, R, HIST>(P, pool, c0, r, f.x, f.y, ok);
     }
     if (tail != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
         const uint2 pr1 = *tail;
-        set_key<WB, R>(P, pool, c0, r, pr1.x, bip_hash(P, pr1.y), true);
+        set_key<WB, R, HIST>(P, pool, c0, r, pr1.x, bip_hash(P, pr1.y), true);
     }
 }
 
@@ -256,7 +292,8 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
                         (size_t)INGEST_WARPS * (QCAP + (P.keys ? Q2CAP : 0)) * sizeof(uint2);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        auto kern = P.r == 4 ? ingest_kernel<WB, 4> : ingest_kernel<WB, 0>;
+        auto kern = P.hist ? (P.r == 4 ? ingest_kernel<WB, 4, true> : ingest_kernel<WB, 0, true>)
+                           : (P.r == 4 ? ingest_kernel<WB, 4, false> : ingest_kernel<WB, 0, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;

@@ -36,7 +36,20 @@ struct Params {
     // the L2 cache.
     unsigned long long *keys;
     uint32_t klg;
+    // ASSE_COUNTER_AT_HIST: per ATV, the ATs last set in each slice phase
+    // t mod 2k, phase-major ([2k][r * E] 16-bit counts); null otherwise.
+    uint16_t *hist;
 };
+
+// Add delta to the 16-bit count hist[i] (a 32-bit atomic on the word that
+// holds it; a count stays in 0..g, so its neighbour never sees a carry).
+#ifdef __CUDACC__
+__device__ __forceinline__ void hist_add(uint16_t *hist, uint64_t i, int delta)
+{
+    uint32_t *w = reinterpret_cast<uint32_t *>(hist + (i & ~1ull));
+    atomicAdd(w, (uint32_t)delta << (16 * (uint32_t)(i & 1)));
+}
+#endif
 
 // Bits of one counter field in the packed words: the counter's own width,
 // ceil(log2(2k+1)) for timestamps (values 0..2k, Sec. 3) or ceil(log2(k+1))
@@ -255,6 +268,15 @@ cudaError_t launch_restore(const Params &P, const ScanOut &o, Tuple *scratch, ui
 cudaError_t launch_estimate(const Params &P, uint32_t w, const uint32_t *pool, uint32_t c0, uint32_t kp,
                             const unsigned long long *aat, const uint32_t *aips, uint64_t n, asse_superpoint *out,
                             int sms, cudaStream_t s, uint64_t *launches);
+
+// ASSE_COUNTER_AT_HIST (asse_hist.cu): the scan of a pool with slice counts
+// (|ATV|^{k'} from the counts of the k' latest phases, row-frame loads,
+// super ATVs and their masks from their words), and the rebuild of the
+// counts from the pool's words (asse_load).
+cudaError_t launch_hist_scan(const Params &P, uint32_t w, const uint32_t *pool, uint32_t kp, const SliceCtl *ctl,
+                             const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches);
+cudaError_t launch_hist_rebuild(const Params &P, uint32_t w, const uint32_t *pool, const SliceCtl *ctl, int sms,
+                                cudaStream_t s, uint64_t *launches);
 
 // At least n_reads random 4-byte reads of buf[0, n_words) on stream s, with
 // every SM busy (asse_probe.cu); *issued receives the number launched.

@@ -40,8 +40,10 @@ namespace asse {
 
 namespace {
 
-constexpr int SCAN_THREADS = 640;  // 20 warps: at most 102 registers a thread
-constexpr int SCAN_WARPS = SCAN_THREADS / 32;
+// Threads of a scan CTA: 20 warps for the interleaved layout (4 KB tiles of
+// wide ATVs, at most 102 registers a thread), 16 for the segment layouts,
+// whose code needs more registers.
+constexpr int scan_threads(bool ilv) { return ilv ? 640 : 512; }
 
 // ---------------------------------------------------------------- scan kernel
 
@@ -52,7 +54,7 @@ constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 // ILV: the interleaved tile layout (G.ilv), fixed at compile time so that
 // the per-word index arithmetic of the inner loop has no layout branch.
 template <int WB, bool FUSE, int NW, bool BG, bool ILV>
-__global__ void __launch_bounds__(SCAN_THREADS, 1) scan_kernel(Params P, uint32_t *pool, const ScanWindows W,
+__global__ void __launch_bounds__(scan_threads(ILV), 1) scan_kernel(Params P, uint32_t *pool, const ScanWindows W,
                                                                const SliceCtl *ctl, uint32_t total_atv, ScanGeom G)
 {
     static_assert(!BG || WB == 8, "the in-field guard needs byte-wide fields");
@@ -363,6 +365,13 @@ __global__ void __launch_bounds__(256) refresh_kernel(Params P, uint32_t *pool, 
     const uint64_t nw = nw0 + nw1;
     const uint64_t total = (uint64_t)total_atv * nw;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (P.hist) {
+        // the slice counts of the opening slice's phase start again from zero:
+        // every AT they counted (set 2k slices ago) has been cleared by now
+        uint16_t *hz = P.hist + (uint64_t)R.c0n * total_atv;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_atv; i += stride)
+            hz[i] = 0;
+    }
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
         const uint64_t atv = idx / nw;
         const uint32_t kq = (uint32_t)(idx - atv * nw);
@@ -422,7 +431,7 @@ ScanGeom scan_geometry(uint32_t Wd, uint32_t mw, uint32_t nw, size_t smem_limit)
         const size_t h = fixed + 2 * warps * sizeof(uint64_t) + (size_t)warps * mw * 4;
         return (h + 127) / 128 * 128;
     };
-    G.warps = SCAN_WARPS;
+    G.warps = scan_threads(G.ilv) / 32;
     while (G.warps > 1 && head(G.warps) + (size_t)G.warps * 2 * G.tile_words * 4 > smem_limit)
         G.warps--;
     G.tile_offset = (uint32_t)head(G.warps);
@@ -466,7 +475,7 @@ cudaError_t launch_scan_nw(const Params &P, uint32_t w, uint32_t *pool, const Sc
             return e;
         const uint64_t want = (ntiles + G.warps - 1) / G.warps;
         const unsigned grid = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
-        kern<<<grid, SCAN_THREADS, G.smem, s>>>(P, pool, W, ctl, total, G);
+        kern<<<grid, scan_threads(G.ilv), G.smem, s>>>(P, pool, W, ctl, total, G);
         return cudaGetLastError();
     });
 }

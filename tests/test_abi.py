@@ -53,7 +53,7 @@ def _cfg(**kw):
     (dict(k=0), "k must"), (dict(k=128), "k must"), (dict(g=19, k=10), "g must"), (dict(g=5000), "g must"),
     (dict(r=1), "r must"), (dict(r=9), "r must"), (dict(c=17), "c <= 16"), (dict(u=9), "u <= 8"),
     (dict(s=0), "s <= c"), (dict(s=13), "s <= c"), (dict(s=3), "completeness"), (dict(A=1), "A must"),
-    (dict(bh_a=2), "odd"), (dict(counter=3), "counter"), (dict(theta=0), "theta"),
+    (dict(bh_a=2), "odd"), (dict(counter=4), "counter"), (dict(theta=0), "theta"),
     (dict(key_table=3), "key_table"), (dict(pad=1), "key_table"),
     (dict(c=12, u=4, s=10), "s*(r-1) < 32-u"), (dict(k=100, g=4000), "512 words"),
 ])

@@ -1,8 +1,9 @@
 """Parity at the full size of the long-window workload (k=60, 32 Mi pairs
 per slice, 4 x 262,144 ATVs of g=1024 ATs: a 1 GB AT pool, 0.87 GB with
-aging counters), for the first two slices, with both counter kinds: the
+aging counters), for the first two slices, with each counter kind: the
 state after ingest and after the refresh, counts, loads, candidates and
-report against the oracle."""
+report against the oracle (timestamps, aging counters, and timestamps with
+slice counts)."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,7 @@ def long_slices():
     return w, [w.pairs(t) for t in range(2)]
 
 
-@pytest.mark.parametrize("counter", ["at", "ace"])
+@pytest.mark.parametrize("counter", ["at", "ace", "hist"])
 def test_long_full_size_two_slices(mods, long_slices, counter):
     asse, oracle, torch = mods
     w, slices = long_slices

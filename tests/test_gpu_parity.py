@@ -86,14 +86,19 @@ CASES = [
     # one ACT for the whole ATV: the refresh reaches every word every k slices
     (1, 37, 4, 8, 0, 8, "aligned"), (4, 130, 4, 9, 2, 7, "aligned"), (10, 512, 4, 8, 0, 8, "aligned"),
     (12, 1024, 4, 8, 0, 8, "aligned"),
+    # timestamps with slice counts: the close counts from the counts kept by the ingest
+    (1, 37, 4, 8, 0, 8, "hist"), (3, 61, 3, 11, 1, 10, "hist"), (5, 130, 5, 7, 1, 6, "hist"),
+    (10, 211, 4, 9, 2, 7, "hist"), (40, 257, 4, 8, 0, 8, "hist"),
 ]
+
+MODE = {"at": 0, "ace": 1, "aligned": 2, "hist": 0}
 
 @pytest.mark.parametrize("k,g,r,c,u,s,counter", CASES)
 def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
     asse, oracle, torch = mods
     theta = max(4, g // 3)
     p = _params(k, g, r, c, u, s, theta, seed=k + g)
-    mode = {"at": 0, "ace": 1, "aligned": 2}[counter]
+    mode = MODE[counter]
     # half of the cases with the ingest's key table (small pools have none by default)
     pool = asse.Pool(p, counter=counter, restore_cap=1 << 14, key_table="on" if (k + g) % 2 else "auto")
     orc = oracle.Oracle.from_params(p, mode=mode)
@@ -117,7 +122,7 @@ def test_random_configs_every_slice(mods, k, g, r, c, u, s, counter):
 # in byte-wide fields, four to a word, or 6-bit aging counters) with g = 1024
 # (an ATV of 256 words, scanned by eight lanes), and k = 30 (6-bit / 5-bit).
 EDGE_CASES = [(60, 1024, 4, 8, 1, 8, "at"), (60, 1024, 4, 8, 1, 8, "ace"), (60, 1024, 4, 8, 1, 8, "aligned"),
-              (30, 512, 4, 9, 2, 7, "at"), (30, 512, 4, 9, 2, 7, "ace")]
+              (60, 1024, 4, 8, 1, 8, "hist"), (30, 512, 4, 9, 2, 7, "at"), (30, 512, 4, 9, 2, 7, "ace")]
 
 
 @pytest.mark.parametrize("k,g,r,c,u,s,counter", EDGE_CASES)
@@ -131,7 +136,7 @@ def test_window_edges_full_cycle(mods, k, g, r, c, u, s, counter):
     asse, oracle, torch = mods
     theta = g // 3
     p = _params(k, g, r, c, u, s, theta, seed=k + 3 * g)
-    mode = {"at": 0, "ace": 1, "aligned": 2}[counter]
+    mode = MODE[counter]
     pool = asse.Pool(p, counter=counter, restore_cap=1 << 12)
     orc = oracle.Oracle.from_params(p, mode=mode)
     rng = np.random.default_rng(k * 7 + g)
@@ -270,6 +275,44 @@ def test_host_ingest_chunks_and_snapshot(mods):
     assert ei.value.status == asse.EINVAL
 
 
+def test_slice_counts_stepwise_and_snapshot(mods):
+    """A pool with slice counts: the stepwise calls (scan, restore, estimate,
+    advance) give the oracle's counts, candidates and estimates, and a
+    snapshot loaded into a fresh pool (whose counts are rebuilt from the
+    words) continues with the same counts and reports as the original."""
+    asse, oracle, torch = mods
+    p = _params(6, 150, 4, 9, 2, 7, 60, seed=15)
+    a = asse.Pool(p, counter="hist")
+    orc = oracle.Oracle.from_params(p)
+    for t in range(15):
+        pairs = mixed_pairs(15, t, 4001, [30, 60, 120, 400])
+        a.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        kp = 1 + t % 6
+        a.scan(kp)
+        np.testing.assert_array_equal(a.counts(), orc.counts(kp), err_msg=f"t={t}")
+        a.restore()
+        res = orc.close_report(kp)
+        compare_lists(a.candidates(), res["candidates"], p["theta"], "csip t=%d" % t)
+        a.advance()
+        orc.advance()
+        np.testing.assert_array_equal(state(a), orc.at(), err_msg=f"after refresh t={t}")
+    b = asse.Pool(p, counter="hist")
+    b.load(a.snapshot())
+    for t in range(15, 30):
+        pairs = mixed_pairs(15, t, 4001, [30, 60, 120, 400])
+        for pl in (a, b):
+            pl.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        res = check_close(b, orc, 6)
+        a.close_slice(6)
+        np.testing.assert_array_equal(a.counts(), b.counts())
+        compare_lists(a.report(), res["report"], p["theta"], "report t=%d" % t)
+        orc.advance()
+    for pl in (a, b):
+        pl.close()
+
+
 def test_key_table_repeats_and_slice_wrap(mods):
     """The ingest skips a (aip, BH(bip)) key already set in the open slice,
     remembered in a key table shared by all blocks and tagged with the low 32
@@ -390,7 +433,7 @@ def test_link_full_size_three_slices(mods):
 @pytest.mark.parametrize("k,g,r,c,u,s,counter,n_win", [
     (6, 150, 4, 9, 2, 7, "at", 3), (10, 211, 4, 9, 2, 7, "at", 4), (5, 77, 5, 7, 1, 6, "ace", 4),
     (1, 64, 4, 8, 0, 8, "ace", 2), (20, 97, 8, 6, 2, 4, "at", 2), (40, 257, 4, 8, 0, 8, "at", 4),
-    (10, 570, 4, 8, 0, 8, "ace", 3), (60, 1024, 4, 8, 1, 8, "at", 3)])
+    (10, 570, 4, 8, 0, 8, "ace", 3), (60, 1024, 4, 8, 1, 8, "at", 3), (10, 211, 4, 9, 2, 7, "hist", 4)])
 def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
     """One pass over the pool for several windows k' <= k: every window's
     counts, loads, candidates and report equal the oracle's close for that
@@ -399,7 +442,7 @@ def test_multi_window_close(mods, k, g, r, c, u, s, counter, n_win):
     theta = max(4, g // 3)
     p = _params(k, g, r, c, u, s, theta, seed=3 * k + g)
     pool = asse.Pool(p, counter=counter, restore_cap=1 << 14)
-    orc = oracle.Oracle.from_params(p, mode=1 if counter == "ace" else 0)
+    orc = oracle.Oracle.from_params(p, mode=MODE[counter])
     heavy = [theta // 2, theta, 2 * theta, 3 * theta]
     rng = np.random.default_rng(k + 7 * g)
     for t in range(2 * k + 3):
