@@ -328,21 +328,12 @@ int pool_enqueue_close(asse_pool *p, uint32_t kp, bool timed)
         return rc;
     if (timed)
         CK(p, cudaEventRecord(p->tev[0], p->stream));
-    if (p->P.hist) {
-        // counts from the slice counts; the refresh (with the zeroing of the
-        // next slice's counts) runs after the restore, then the next slice opens
-        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
-        if (timed)
-            CK(p, cudaEventRecord(p->tev[1], p->stream));
-        CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
-                             &p->launches));
-        CK(p, launch_refresh(p->P, p->w, p->pool, p->ctl, p->sms, p->stream, &p->launches));
-        CK(p, launch_advance_ctl(p->P, p->ctl, p->stream, &p->launches));
-        if (timed)
-            CK(p, cudaEventRecord(p->tev[2], p->stream));
-        return ASSE_OK;
-    }
-    CK(p, launch_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    // counts from the slice counts, or from every AT; either way with the
+    // refresh for the next slice fused in
+    if (p->P.hist)
+        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+    else
+        CK(p, launch_scan(p->P, p->w, p->pool, kp, true, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     if (timed)
         CK(p, cudaEventRecord(p->tev[1], p->stream));
     CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
@@ -357,7 +348,8 @@ int pool_enqueue_scan(asse_pool *p, uint32_t kp)
     if (int rc = reset_close_state(p))
         return rc;
     if (p->P.hist)
-        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
+        CK(p, launch_hist_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream,
+                               &p->launches));
     else
         CK(p, launch_scan(p->P, p->w, p->pool, kp, false, p->ctl, scan_out(p), p->sms, p->stream, &p->launches));
     return ASSE_OK;
@@ -801,7 +793,8 @@ int asse_close_slice_multi(asse_pool *p, const uint32_t *kps, uint32_t n_windows
         // one count pass per window over the slice counts, then the restores,
         // the refresh (with the zeroing of the next slice's counts) and the next slice
         for (uint32_t m = 0; m < n_windows; m++)
-            CK(p, launch_hist_scan(p->P, p->w, p->pool, kps[m], p->ctl, W.o[m], p->sms, p->stream, &p->launches));
+            CK(p, launch_hist_scan(p->P, p->w, p->pool, kps[m], false, p->ctl, W.o[m], p->sms, p->stream,
+                                   &p->launches));
         for (uint32_t m = 0; m < n_windows; m++)
             CK(p, launch_restore(p->P, W.o[m], p->scratch, p->cap, list_w(p, m, false), list_w(p, m, true),
                                  p->out_cap, p->stream, &p->launches));

@@ -7,9 +7,10 @@
 // phase, coalesced across the ATVs (the counts are phase-major), instead of
 // the whole ATV.  The row-frame loads and the super-ATV lists follow as in
 // the full scan; only a super ATV's words are read, to build its g-bit active
-// mask for Algorithm 5.  The refresh of the two checked blocks (Algorithm 2)
-// runs in the standalone refresh kernel, which also zeroes the counts of the
-// opening slice's phase.
+// mask for Algorithm 5.  In the close of a slice the same kernel then runs
+// the refresh of the two checked blocks (Algorithm 2) and zeroes the counts
+// of the opening slice's phase; the stepwise scan leaves both to the refresh
+// kernel of asse_advance.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,74 +25,139 @@ namespace {
 constexpr int HIST_THREADS = 256;
 constexpr int HIST_WARPS = HIST_THREADS / 32;
 
-template <int WB>
-__global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, const uint32_t *pool, uint32_t kp,
+// V ATVs per thread (8: one 16-byte load per phase, the ATVs of one thread
+// in one row-frame; 1 for pools with fewer than 8 columns).  FUSE: the close
+// of a slice, which also runs Algorithm 2 on the two checked blocks of each
+// of the thread's ATVs (after the warp has built the masks of its super
+// ATVs from the unrefreshed words) and zeroes the counts of the opening
+// slice's phase (not a phase of the window being counted).
+template <int WB, bool FUSE, int V>
+__global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint32_t *pool, uint32_t kp,
                                                                  const SliceCtl *ctl, ScanOut o, uint32_t total_atv)
 {
     constexpr uint32_t F = 32 / WB;
     extern __shared__ __align__(16) uint8_t hsm[];
-    RangeDesc *desc = reinterpret_cast<RangeDesc *>(hsm);                  // [Wd]
-    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(desc + P.Wd);         // [warps][mw]
+    RangeDesc *desc = reinterpret_cast<RangeDesc *>(hsm);                  // [Wd] count ranges
+    RangeDesc *rdesc = desc + P.Wd;                                        // [Wd] refresh ranges (FUSE)
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(rdesc + (FUSE ? P.Wd : 0));  // [warps][mw]
     const uint32_t c0 = ctl->c0;
+    const Refresh R = ctl->R;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x)
+    for (uint32_t q = threadIdx.x; q < P.Wd; q += blockDim.x) {
         desc[q] = count_desc<WB>(P, q, c0, kp);
+        if (FUSE)
+            rdesc[q] = refresh_desc<WB>(P, q, R.c0n);
+    }
     __syncthreads();
     uint32_t *my_mask = maskbuf + warp * P.mw;
     const uint32_t cols = P.cmask + 1;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < total_atv; base += stride) {
-        const uint64_t atv = base + lane;
-        const bool mine = atv < total_atv;
-        uint32_t c = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * V;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + warp * 32u) * V; base < total_atv; base += stride) {
+        const uint64_t a0 = base + (uint64_t)lane * V;
+        const bool mine = a0 < total_atv;
+        uint32_t c[V];
+#pragma unroll
+        for (int v = 0; v < V; v++)
+            c[v] = 0;
         if (mine) {
             // phases c0, c0-1, ..., c0-k'+1 (mod 2k): the slices of the window
             uint32_t ph = c0;
             for (uint32_t a = 0; a < kp; a++) {
-                c += P.hist[(uint64_t)ph * total_atv + atv];
+                const uint16_t *row = P.hist + (uint64_t)ph * total_atv + a0;
+                if constexpr (V == 8) {
+                    const uint4 h = *reinterpret_cast<const uint4 *>(row);
+                    c[0] += h.x & 0xffffu;
+                    c[1] += h.x >> 16;
+                    c[2] += h.y & 0xffffu;
+                    c[3] += h.y >> 16;
+                    c[4] += h.z & 0xffffu;
+                    c[5] += h.z >> 16;
+                    c[6] += h.w & 0xffffu;
+                    c[7] += h.w >> 16;
+                } else {
+                    c[0] += row[0];
+                }
                 ph = ph == 0 ? P.k2 - 1 : ph - 1;
             }
-            o.cnt[atv] = (uint16_t)c;
+            if constexpr (V == 8) {
+                *reinterpret_cast<uint4 *>(o.cnt + a0) =
+                    make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+            } else {
+                o.cnt[a0] = (uint16_t)c[0];
+            }
         }
-        const uint32_t sg = mine ? (uint32_t)(atv >> P.c) : 0xffffffffu;  // row * 2^u + frame
+        // the V ATVs of a thread share a row-frame (2^c is a multiple of V)
+        const uint32_t sg = mine ? (uint32_t)(a0 >> P.c) : 0xffffffffu;  // row * 2^u + frame
         const unsigned grp = __match_any_sync(FULL_MASK, sg);
         {
-            const uint32_t s = __reduce_add_sync(grp, mine ? c : 0u);
+            uint32_t sum = 0;
+#pragma unroll
+            for (int v = 0; v < V; v++)
+                sum += c[v];
+            const uint32_t s = __reduce_add_sync(grp, mine ? sum : 0u);
             if (mine && (uint32_t)(__ffs(grp) - 1) == lane && s)
                 atomicAdd(&o.aat[sg], (unsigned long long)s);
         }
-        const bool sup = mine && c >= P.T;
-        uint32_t slot = 0;
-        if (sup) {
-            slot = atomicAdd(&o.sa_n[sg], 1u);
-            o.sa_x[(size_t)sg * cols + slot] = (uint32_t)atv & P.cmask;
-        }
-        unsigned sbits = __ballot_sync(FULL_MASK, sup);
-        while (sbits) {
-            // the g-bit active mask of one super ATV from its words
-            const uint32_t hl = __ffs(sbits) - 1;
-            sbits &= sbits - 1;
-            const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
-            const uint64_t atv_a = base + hl;
-            const uint32_t sg_a = (uint32_t)(atv_a >> P.c);
-            for (uint32_t k = lane; k < P.mw; k += 32)
-                my_mask[k] = 0;
-            __syncwarp();
-            for (uint32_t q = lane; q < P.Wd; q += 32) {
-                const uint32_t word = pool[atv_a * P.Wd + q];
-                const uint32_t am = field_bits<WB>(word, desc[q]);
-                if (am) {
-                    const uint32_t pos = q * F, off = pos & 31;
-                    atomicOr(&my_mask[pos >> 5], am << off);
-                    if (off + F > 32 && (am >> (32 - off)))
-                        atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
-                }
+#pragma unroll 1
+        for (int v = 0; v < V; v++) {
+            uint32_t cv = 0;
+#pragma unroll
+            for (int vv = 0; vv < V; vv++)
+                if (vv == v)
+                    cv = c[vv];
+            const bool sup = mine && cv >= P.T;
+            uint32_t slot = 0;
+            if (sup) {
+                slot = atomicAdd(&o.sa_n[sg], 1u);
+                o.sa_x[(size_t)sg * cols + slot] = (uint32_t)(a0 + v) & P.cmask;
             }
-            __syncwarp();
-            uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
-            for (uint32_t k = lane; k < P.mw; k += 32)
-                dst[k] = my_mask[k];
-            __syncwarp();
+            unsigned sbits = __ballot_sync(FULL_MASK, sup);
+            while (sbits) {
+                // the g-bit active mask of one super ATV from its words
+                const uint32_t hl = __ffs(sbits) - 1;
+                sbits &= sbits - 1;
+                const uint32_t slot_a = __shfl_sync(FULL_MASK, slot, hl);
+                const uint64_t atv_a = base + (uint64_t)hl * V + v;
+                const uint32_t sg_a = (uint32_t)(atv_a >> P.c);
+                for (uint32_t k = lane; k < P.mw; k += 32)
+                    my_mask[k] = 0;
+                __syncwarp();
+                for (uint32_t q = lane; q < P.Wd; q += 32) {
+                    const uint32_t word = pool[atv_a * P.Wd + q];
+                    const uint32_t am = field_bits<WB>(word, desc[q]);
+                    if (am) {
+                        const uint32_t pos = q * F, off = pos & 31;
+                        atomicOr(&my_mask[pos >> 5], am << off);
+                        if (off + F > 32 && (am >> (32 - off)))
+                            atomicOr(&my_mask[(pos >> 5) + 1], am >> (32 - off));
+                    }
+                }
+                __syncwarp();
+                uint32_t *dst = o.sa_mask + ((size_t)sg_a * cols + slot_a) * P.mw;
+                for (uint32_t k = lane; k < P.mw; k += 32)
+                    dst[k] = my_mask[k];
+                __syncwarp();
+            }
+        }
+        if (FUSE && mine) {
+            // Algorithm 2 for the next slice on the words of the two checked
+            // blocks of each ATV, and the counts of the opening phase zeroed
+#pragma unroll 1
+            for (int v = 0; v < V; v++) {
+                uint32_t *atw = pool + (a0 + v) * P.Wd;
+                for (uint32_t rr = 0; rr < R.n_ranges; rr++)
+                    for (uint32_t q = R.q_lo[rr]; q <= R.q_hi[rr]; q++) {
+                        const uint32_t w = atw[q];
+                        const uint32_t nw = refresh_swar<WB>(P, w, rdesc[q]);
+                        if (nw != w)
+                            atw[q] = nw;
+                    }
+            }
+            uint16_t *hz = P.hist + (uint64_t)R.c0n * total_atv + a0;
+            if constexpr (V == 8)
+                *reinterpret_cast<uint4 *>(hz) = make_uint4(0, 0, 0, 0);
+            else
+                hz[0] = 0;
         }
     }
 }
@@ -128,22 +194,26 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_rebuild_kernel(Params P, co
 
 }  // namespace
 
-cudaError_t launch_hist_scan(const Params &P, uint32_t w, const uint32_t *pool, uint32_t kp, const SliceCtl *ctl,
+cudaError_t launch_hist_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
                              const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches)
 {
     const uint32_t total = P.r << P.E_log2;
-    const size_t smem = (size_t)P.Wd * sizeof(RangeDesc) + (size_t)HIST_WARPS * P.mw * sizeof(uint32_t);
+    const size_t smem = (size_t)P.Wd * sizeof(RangeDesc) * (fuse ? 2 : 1) + (size_t)HIST_WARPS * P.mw * sizeof(uint32_t);
+    // 8 ATVs a thread when a row-frame holds a multiple of 8 of them
+    const bool v8 = (P.cmask + 1) % 8 == 0;
     *launches += 1;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        cudaError_t e = cudaFuncSetAttribute(hist_scan_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        auto kern = fuse ? (v8 ? hist_scan_kernel<WB, true, 8> : hist_scan_kernel<WB, true, 1>)
+                         : (v8 ? hist_scan_kernel<WB, false, 8> : hist_scan_kernel<WB, false, 1>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        const uint64_t want = (total + HIST_THREADS - 1) / HIST_THREADS;
-        const uint64_t full = (uint64_t)sms * resident_blocks(hist_scan_kernel<WB>, HIST_THREADS, smem);
-        hist_scan_kernel<WB><<<(unsigned)(want < full ? want : full), HIST_THREADS, smem, s>>>(P, pool, kp, ctl, o,
-                                                                                             total);
+        const uint32_t per = v8 ? 8 : 1;
+        const uint64_t want = (total / per + HIST_THREADS - 1) / HIST_THREADS;
+        const uint64_t full = (uint64_t)sms * resident_blocks(kern, HIST_THREADS, smem);
+        kern<<<(unsigned)(want < full ? (want < 1 ? 1 : want) : full), HIST_THREADS, smem, s>>>(P, pool, kp, ctl, o,
+                                                                                           total);
         return cudaGetLastError();
     });
 }

@@ -273,7 +273,9 @@ cudaError_t launch_estimate(const Params &P, uint32_t w, const uint32_t *pool, u
 // (|ATV|^{k'} from the counts of the k' latest phases, row-frame loads,
 // super ATVs and their masks from their words), and the rebuild of the
 // counts from the pool's words (asse_load).
-cudaError_t launch_hist_scan(const Params &P, uint32_t w, const uint32_t *pool, uint32_t kp, const SliceCtl *ctl,
+// fuse: the close of a slice (refresh of the checked blocks and zeroing of
+// the opening phase's counts in the same pass).
+cudaError_t launch_hist_scan(const Params &P, uint32_t w, uint32_t *pool, uint32_t kp, bool fuse, const SliceCtl *ctl,
                              const ScanOut &o, int sms, cudaStream_t s, uint64_t *launches);
 cudaError_t launch_hist_rebuild(const Params &P, uint32_t w, const uint32_t *pool, const SliceCtl *ctl, int sms,
                                 cudaStream_t s, uint64_t *launches);

@@ -2,13 +2,15 @@
 // ATV states, synthetic training states, and the MLP (FEAT -> 256 -> 256 -> 1,
 // ReLU) with its training step, all in the library's own kernels.
 //
-// Matrix products run on the tensor cores through mma.sync m16n8k16 with BF16
-// operands and FP32 accumulation, in one tiled kernel whose operands are
-// addressed by (row, k) strides, so every product of the forward and backward
-// pass (including the transposed ones of the weight gradients, split over
-// the batch) is the same kernel with a different epilogue: bias + ReLU ->
-// BF16, bias + ReLU + dot with w3 (the last layer fused into the second),
-// gradient masked by the ReLU -> BF16, or FP32 atomic accumulation.
+// Every matrix product of the training pass runs on the 5th-generation tensor
+// cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory) through
+// one kernel whose operands are addressed by (row, k) strides
+// (launch_tc_gemm, asse_mlp_tc.cu), so the forward products and the
+// transposed ones of the weight gradients (split over the batch) are the same
+// kernel with a different epilogue: bias + ReLU -> BF16, bias + ReLU + dot
+// with w3 (the last layer fused into the second), gradient masked by the
+// ReLU -> BF16, or FP32 atomic accumulation.  Inference has its own fused
+// tcgen05 kernel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -161,174 +163,6 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
         }
         __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------- GEMM
-
-// Operand addressed by strides: element (i, kk) at p[i * si + kk * sk].
-struct Operand {
-    const bf16 *p;
-    long si, sk;
-};
-
-__device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// out = bf16(relu(v + bias[n]))
-struct EpiBiasRelu {
-    const float *bias;
-    bf16 *out;
-    int ld;
-    static constexpr bool kRowDot = false;
-    __device__ void operator()(int m, int n, float v) const
-    {
-        out[(long)m * ld + n] = __float2bfloat16_rn(fmaxf(v + bias[n], 0.0f));
-    }
-};
-
-// h = bf16(relu(v + bias[n])) stored, and y[m] += h * w3[n]
-struct EpiBiasReluDot {
-    const float *bias;
-    const float *w3;
-    bf16 *out;  // may be null (inference)
-    int ld;
-    float *y;
-    static constexpr bool kRowDot = true;
-    __device__ float operator()(int m, int n, float v) const
-    {
-        const bf16 h = __float2bfloat16_rn(fmaxf(v + bias[n], 0.0f));
-        if (out)
-            out[(long)m * ld + n] = h;
-        return __bfloat162float(h) * w3[n];
-    }
-};
-
-// out = bf16(v) where the forward activation was positive, else 0
-struct EpiReluGrad {
-    const bf16 *act;
-    bf16 *out;
-    int ld;
-    static constexpr bool kRowDot = false;
-    __device__ void operator()(int m, int n, float v) const
-    {
-        const float a = __bfloat162float(act[(long)m * ld + n]);
-        out[(long)m * ld + n] = __float2bfloat16_rn(a > 0.0f ? v : 0.0f);
-    }
-};
-
-// out[m][n] += v (split over the reduction dimension)
-struct EpiAtomic {
-    float *out;
-    int ld;
-    static constexpr bool kRowDot = false;
-    __device__ void operator()(int m, int n, float v) const { atomicAdd(&out[(long)m * ld + n], v); }
-};
-
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
-
-// C[M][N] = sum_k A(m, k) B(n, k); blockIdx.z takes the k range
-// [z * kchunk, (z+1) * kchunk).  4 warps, each a 32 x 32 block of the 64 x 64
-// tile as 2 x 4 m16n8k16 products per 16-wide k step.
-template <class Epi>
-__global__ void __launch_bounds__(128) gemm_kernel(Operand A, Operand B, int M, int N, int K, int kchunk, Epi epi)
-{
-    __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int e = 0; e < 4; e++)
-                acc[i][j][e] = 0.0f;
-    const bool a_kfast = A.sk == 1, b_kfast = B.sk == 1;
-    for (int k0 = kb; k0 < ke; k0 += GBK) {
-        for (int e = tid; e < GBM * GBK; e += 128) {
-            const int r = a_kfast ? e / GBK : e % GBM, c = a_kfast ? e % GBK : e / GBM;
-            const int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < ke) ? A.p[(long)m * A.si + (long)k * A.sk] : __float2bfloat16_rn(0.0f);
-        }
-        for (int e = tid; e < GBN * GBK; e += 128) {
-            const int r = b_kfast ? e / GBK : e % GBN, c = b_kfast ? e % GBK : e / GBN;
-            const int n = n0 + r, k = k0 + c;
-            Bs[r][c] = (n < N && k < ke) ? B.p[(long)n * B.si + (long)k * B.sk] : __float2bfloat16_rn(0.0f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int r = wm * 32 + i * 16 + g;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int r = wn * 32 + j * 8 + g;
-                bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + 2 * t]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[r][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
-    }
-    // element e of acc[i][j]: row g (+8 for e >= 2), column 2t + (e & 1)
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int m = m0 + wm * 32 + i * 16 + g + 8 * h;
-            float dot = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const int n = n0 + wn * 32 + j * 8 + 2 * t + e;
-                    if (m < M && n < N) {
-                        if constexpr (Epi::kRowDot)
-                            dot += epi(m, n, acc[i][j][2 * h + e]);
-                        else
-                            epi(m, n, acc[i][j][2 * h + e]);
-                    }
-                }
-            }
-            if constexpr (Epi::kRowDot) {
-                // the four threads of a row hold its 32 columns of this warp
-                dot += __shfl_xor_sync(FULL_MASK, dot, 1);
-                dot += __shfl_xor_sync(FULL_MASK, dot, 2);
-                if (t == 0 && m < M)
-                    atomicAdd(&epi.y[m], dot);
-            }
-        }
-    }
-}
-
-template <class Epi>
-cudaError_t gemm(Operand A, Operand B, int M, int N, int K, int splits, Epi epi, cudaStream_t s, uint64_t *launches)
-{
-    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
-    const dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, (K + kchunk - 1) / kchunk);
-    *launches += 1;
-    gemm_kernel<Epi><<<grid, 128, 0, s>>>(A, B, M, N, K, kchunk, epi);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- elementwise
@@ -498,10 +332,13 @@ int forward(asse_mlp *m, const bf16 *x, uint64_t n, float *y, bool keep)
     MCK(m, cudaGetLastError());
     fill_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, m->stream>>>(y, n, P + OFF_B3);
     m->launches++;
-    MCK(m, gemm(Operand{x, FEAT, 1}, Operand{m->w1b, FEAT, 1}, (int)n, HID, FEAT, 1,
-                EpiBiasRelu{P + OFF_B1, m->H1, HID}, m->stream, &m->launches));
-    MCK(m, gemm(Operand{m->H1, HID, 1}, Operand{m->w2b, HID, 1}, (int)n, HID, HID, 1,
-                EpiBiasReluDot{P + OFF_B2, P + OFF_W3, keep ? m->H2 : nullptr, HID, y}, m->stream, &m->launches));
+    MCK(m, launch_tc_gemm(TcOperand{x, FEAT, 1}, TcOperand{m->w1b, FEAT, 1}, (int)n, HID, FEAT, 1,
+                          TcEpi{TE_BIAS_RELU, P + OFF_B1, nullptr, nullptr, m->H1, nullptr, nullptr, HID}, m->error,
+                          m->stream, &m->launches));
+    MCK(m, launch_tc_gemm(TcOperand{m->H1, HID, 1}, TcOperand{m->w2b, HID, 1}, (int)n, HID, HID, 1,
+                          TcEpi{TE_BIAS_RELU_DOT, P + OFF_B2, P + OFF_W3, nullptr, keep ? m->H2 : nullptr, nullptr, y,
+                                HID},
+                          m->error, m->stream, &m->launches));
     return ASSE_OK;
 }
 
@@ -521,18 +358,23 @@ int backward(asse_mlp *m, const bf16 *x, const float *t, uint64_t n, float *loss
                                               G + OFF_B3);
     m->launches += 2;
     MCK(m, cudaGetLastError());
-    const int splits = (int)((n + 1023) / 1024);
+    // the weight-gradient products reduce over the batch: split it so that
+    // enough CTAs share the work
+    const int splits = (int)((n + 255) / 256);
     // dW2[o][i] = sum_m dZ2[m][o] H1[m][i]
-    MCK(m, gemm(Operand{m->dZ2, 1, HID}, Operand{m->H1, 1, HID}, HID, HID, (int)n, splits,
-                EpiAtomic{G + OFF_W2, HID}, m->stream, &m->launches));
+    MCK(m, launch_tc_gemm(TcOperand{m->dZ2, 1, HID}, TcOperand{m->H1, 1, HID}, HID, HID, (int)n, splits,
+                          TcEpi{TE_ATOMIC, nullptr, nullptr, nullptr, nullptr, G + OFF_W2, nullptr, HID}, m->error,
+                          m->stream, &m->launches));
     // dZ1 = (dZ2 W2) masked by H1 > 0
-    MCK(m, gemm(Operand{m->dZ2, HID, 1}, Operand{m->w2b, 1, HID}, (int)n, HID, HID, 1,
-                EpiReluGrad{m->H1, m->dZ1, HID}, m->stream, &m->launches));
+    MCK(m, launch_tc_gemm(TcOperand{m->dZ2, HID, 1}, TcOperand{m->w2b, 1, HID}, (int)n, HID, HID, 1,
+                          TcEpi{TE_RELU_GRAD, nullptr, nullptr, m->H1, m->dZ1, nullptr, nullptr, HID}, m->error,
+                          m->stream, &m->launches));
     colsum_kernel<<<rb, HID, 0, m->stream>>>(m->dZ1, n, G + OFF_B1);
     m->launches++;
     // dW1[o][j] = sum_m dZ1[m][o] X[m][j]
-    MCK(m, gemm(Operand{m->dZ1, 1, HID}, Operand{x, 1, FEAT}, HID, FEAT, (int)n, splits,
-                EpiAtomic{G + OFF_W1, FEAT}, m->stream, &m->launches));
+    MCK(m, launch_tc_gemm(TcOperand{m->dZ1, 1, HID}, TcOperand{x, 1, FEAT}, HID, FEAT, (int)n, splits,
+                          TcEpi{TE_ATOMIC, nullptr, nullptr, nullptr, nullptr, G + OFF_W1, nullptr, FEAT}, m->error,
+                          m->stream, &m->launches));
     if (loss_dev)
         MCK(m, cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
     return ASSE_OK;

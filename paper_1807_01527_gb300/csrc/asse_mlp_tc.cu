@@ -400,6 +400,192 @@ __global__ void __launch_bounds__(THREADS, 1)
         atomicExch(error, 1);
 }
 
+// ---------------------------------------------------------------- training GEMMs
+
+// C[M][N] = sum_k A(m, k) B(n, k) for the products of the training pass, on
+// the tensor cores.  One CTA of four warps computes a 128 x BN tile (BN = 64,
+// or N when N is not a multiple of 64; N <= 256, a multiple of 16) over the
+// k range of blockIdx.z; A and B are gathered
+// from global memory through their (row, k) strides into the K-major
+// core-matrix layout in shared memory (the weight-gradient products read
+// their operands transposed), 64 k at a time through two stages; one thread
+// issues the MMAs (M = 128, N, K = 16) into a tensor-memory accumulator and
+// commits each stage to an mbarrier, so the gather of the next stage overlaps
+// the MMAs of this one.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w: rows 32 w ..) and applies the step's fused operation.
+constexpr int TG_THREADS = 128;
+constexpr int TG_KC = 64;                               // k per stage
+constexpr uint32_t TG_A = 128 * TG_KC * 2;              // 16 KB
+constexpr uint32_t TG_B = 256 * TG_KC * 2;              // 32 KB
+constexpr uint32_t TG_BAR = 2 * (TG_A + TG_B);          // 2 stage barriers + final barrier + tmem slot, abort
+constexpr uint32_t TG_SMEM = TG_BAR + 64 + 1024;        // + alignment slack of the base
+constexpr uint32_t TG_TMEM_COLS = 256;
+
+__device__ __forceinline__ void mma_f16_n(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane, waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        v[i] = __uint_as_float(r[i]);
+}
+
+// Gather rows [r0, r0 + rows) x k [k0, k0 + 64) of an operand into the
+// K-major core-matrix layout: element (row, k) at byte
+// (row / 8) * 1024 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2; outside
+// [0, nrows) x [k0, kend) zero.  Rows contiguous in k (sk = 1, 16-byte
+// aligned groups) move as one 16-byte load per 8 k; otherwise each thread
+// takes consecutive rows so that the warp's loads of one k are contiguous
+// when the operand is row-contiguous (si = 1).
+__device__ __forceinline__ void tg_gather(uint8_t *dst, TcOperand op, int r0, int rows, int nrows, int k0, int kend)
+{
+    const bool vec = op.sk == 1 && (op.si % 8) == 0 && (reinterpret_cast<uintptr_t>(op.p) & 15u) == 0;
+    for (int e = threadIdx.x; e < rows * (TG_KC / 8); e += TG_THREADS) {
+        const int row = vec ? e / (TG_KC / 8) : e % rows;
+        const int kg = vec ? e % (TG_KC / 8) : e / rows;
+        const int i = r0 + row, k = k0 + kg * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (i < nrows) {
+            if (vec && k + 8 <= kend) {
+                v = *reinterpret_cast<const uint4 *>(op.p + (long)i * op.si + k);
+            } else {
+                uint16_t h[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    h[j] = k + j < kend ? __bfloat16_as_ushort(op.p[(long)i * op.si + (long)(k + j) * op.sk]) : 0;
+                v = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
+                               h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
+            }
+        }
+        *reinterpret_cast<uint4 *>(dst + (row >> 3) * 1024 + kg * 128 + (row & 7) * 16) = v;
+    }
+}
+
+// The CTA at (x, y, z) computes rows 128 x .. and columns BN y .. BN y + BN - 1
+// over the z-th k range.
+__global__ void __launch_bounds__(TG_THREADS) tc_gemm_kernel(TcOperand A, TcOperand B, int M, int N, int BN, int K,
+                                                             int kchunk, TcEpi epi, int *error)
+{
+    extern __shared__ uint8_t tg_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(tg_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + TG_BAR);  // [0], [1] stages, [2] final
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(bar + 3);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int nchunks = ke > kb ? (ke - kb + TG_KC - 1) / TG_KC : 0;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        tmem_slot[1] = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(const_cast<uint32_t *>(tmem_slot))),
+                     "r"(TG_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot[0];
+    // FP32 accumulator, BF16 A and B, both K-major, N >> 3, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; c++) {
+        const int s = c & 1;
+        // the stage is free once the MMAs of the chunk two back have read it
+        if (c >= 2 && !__syncthreads_and(wait_or_abort(&bar[s], ((c - 2) >> 1) & 1, abort_flag))) {
+            ok = false;
+            break;
+        }
+        uint8_t *sa = sm + s * (TG_A + TG_B), *sb = sa + TG_A;
+        const int k0 = kb + c * TG_KC;
+        tg_gather(sa, A, m0, 128, M, k0, ke);
+        tg_gather(sb, B, n0, BN, N, k0, ke);
+        fence_async_smem();  // the generic stores before the tensor core reads them
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ab = smem_addr(sa), bb = smem_addr(sb);
+#pragma unroll
+            for (int kk = 0; kk < TG_KC / 16; kk++)
+                mma_f16_n(tmem, sdesc(ab + kk * 256, 128, 1024), sdesc(bb + kk * 256, 128, 1024), idesc,
+                          (c > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&bar[s]);
+        }
+    }
+    // every MMA done (or none issued) before the accumulator is read or freed
+    if (tid == 0) {
+        mma_commit(&bar[2]);
+    }
+    const bool done = __syncthreads_and(ok && wait_or_abort(&bar[2], 0, abort_flag));
+    if (!done && tid == 0)
+        mbar_wait(&bar[2], 0);  // bounded: the committed MMAs finish before the free below
+    tc_fence_after();
+    if (done && nchunks > 0) {
+        const int m = m0 + warp * 32 + lane;
+        float dot = 0.0f;
+        for (int cb = 0; cb < BN; cb += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+            if (m >= M)
+                continue;
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int n = n0 + cb + j;
+                if (cb + j >= BN || n >= N)
+                    break;
+                const float a = v[j];
+                if (epi.kind == TE_ATOMIC) {
+                    atomicAdd(&epi.outf[(long)m * epi.ld + n], a);
+                } else if (epi.kind == TE_RELU_GRAD) {
+                    const float act = __bfloat162float(epi.act[(long)m * epi.ld + n]);
+                    epi.out[(long)m * epi.ld + n] = __float2bfloat16_rn(act > 0.0f ? a : 0.0f);
+                } else {
+                    const bf16 h = __float2bfloat16_rn(fmaxf(a + epi.bias[n], 0.0f));
+                    if (epi.out)
+                        epi.out[(long)m * epi.ld + n] = h;
+                    if (epi.kind == TE_BIAS_RELU_DOT)
+                        dot = fmaf(__bfloat162float(h), epi.w3[n], dot);
+                }
+            }
+        }
+        if (epi.kind == TE_BIAS_RELU_DOT && m < M)
+            atomicAdd(&epi.y[m], dot);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TG_TMEM_COLS)
+                     : "memory");
+    if (tid == 0 && (!done || tmem_slot[1] != 0u))
+        atomicExch(error, 1);
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -421,6 +607,23 @@ EncodeTiled encode_fn()
 }
 
 }  // namespace
+
+cudaError_t launch_tc_gemm(TcOperand A, TcOperand B, int M, int N, int K, int splits, const TcEpi &epi, int *error,
+                           cudaStream_t s, uint64_t *launches)
+{
+    if (N < 16 || N > 256 || N % 16 != 0 || M < 1 || K < 1 || splits < 1)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
+    if (e != cudaSuccess)
+        return e;
+    // 64-column tiles where N allows, for more CTAs on the small products of a training batch
+    const int BN = N % 64 == 0 ? 64 : N;
+    const int kchunk = ((K + splits - 1) / splits + TG_KC - 1) / TG_KC * TG_KC;
+    const dim3 grid((M + 127) / 128, (N + BN - 1) / BN, (K + kchunk - 1) / kchunk);
+    tc_gemm_kernel<<<grid, TG_THREADS, TG_SMEM, s>>>(A, B, M, N, BN, K, kchunk, epi, error);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mlp_pack(const float *params, bf16 *w1p, bf16 *w2p, cudaStream_t s, uint64_t *launches)
 {

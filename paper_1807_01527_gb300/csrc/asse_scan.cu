@@ -187,8 +187,9 @@ __global__ void __launch_bounds__(scan_threads(ILV), 1) scan_kernel(Params P, ui
 #pragma unroll
                 for (int m = 0; m < NW; m++) {
                     if (m < (int)nw) {
-                        // the range entries of words q .. q+3: consecutive, or a chunk apart
-                        const uint32_t xq = didx(m, q), dx = ILV ? nchunk : 1u;
+                        // the range entries of words q .. q+3: consecutive (skewed by the
+                        // segment), or a chunk apart (q is a multiple of 4)
+                        const uint32_t xq = m * n_cd + (ILV ? (q >> 2) : q + part), dx = ILV ? nchunk : 1u;
                         if constexpr (BG) {
                             // per-byte counts (at most 64 words per lane: no carry between bytes)
                             cnt[m] += (in_ranges_bytes(x.x, cd_lo[xq]) >> 7) +
