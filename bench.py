@@ -39,10 +39,16 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # the id of the kernel source they were taken from (kernel_source_id below).
 # A figure whose source id no longer matches the current sources is reported
 # as null (the kernel has changed since the capture).
-TRAFFIC = {}
+TRAFFIC = {
+    ("long", "hist", "ingest"): (1366155776, "3c249aac167e"),
+    ("long", "hist", "hist_scan"): (405193216, "127a9855ddab"),
+    ("link", "at", "ingest"): (201392640, "3c249aac167e"),
+    ("link", "at", "scan"): (96309760, "4ee67a1c66a0"),
+}
 KERNEL_SOURCES = {
     "ingest": ["asse_ingest.cu", "asse_device.cuh", "asse_internal.h"],
     "scan": ["asse_scan.cu", "asse_swar.cuh", "asse_bytes.h", "asse_device.cuh", "asse_internal.h", "asse_ptx.cuh"],
+    "hist_scan": ["asse_hist.cu", "asse_swar.cuh", "asse_bytes.h", "asse_device.cuh", "asse_internal.h"],
 }
 
 
@@ -165,7 +171,7 @@ def run_reference(args, w):
     text, cores, orc = "", 1, None
     for i in range(args.warmup + args.steps):
         p = host[i % n_cycled]
-        dt, cores, text, orc = oracle_slice_time(w, p, args.counter, orc)
+        dt, cores, text, orc = oracle_slice_time(w, p, counter_for(args, w), orc)
         if i >= args.warmup:
             times.append(dt)
             pairs_done += p.shape[0]
@@ -450,6 +456,11 @@ def run_serve(args):
         return pool_of_batches[key]
 
     srv = asse.Server(20 << 30)
+    model = None
+    if args.serve_learned:
+        # learned per-ATV inference inside every close graph (one model for all streams)
+        model = asse.MLP(seed=1, stream=torch.cuda.current_stream().cuda_stream)
+        model.set_loss("rel_mse")
     waiting = list(range(n_streams))
     running = {}
     lat, pairs_done, deferred, max_open = [], 0, 0, 0
@@ -458,11 +469,15 @@ def run_serve(args):
     while waiting or running:
         while waiting:
             i = waiting[0]
-            sid = srv.open(streams[i][0], streams[i][0]["k"], max_batch=16 << 20)
+            sp = streams[i][0]
+            ctr = args.counter if args.counter != "auto" else auto_counter(sp["k"], sp["g"], sp["r"], sp["c"] + sp["u"])
+            sid = srv.open(sp, sp["k"], max_batch=16 << 20, counter=ctr)
             if sid is None:
                 deferred += 1
                 break
             waiting.pop(0)
+            if model is not None:
+                srv.attach_model(sid, model, 20 * float(np.log(2.0)))
             running[i] = [sid, 0, 0]          # sid, slices submitted, slices reported
         max_open = max(max_open, len(running))
         progressed = False
@@ -493,11 +508,14 @@ def run_serve(args):
             "mode": "serve", "dtype": "u32", "data": "synthetic",
             "config": {"workload": "16 streams, k in {4,10,30,60}, 2^14..2^18 ATVs/row, g in {128,512,1024}, "
                                    "batches exp(mean 4Mi) clipped [64Ki,16Mi], 20 GB budget",
+                       "counter": args.counter.upper() + (" (slice counts for pools larger than L2)"
+                                                          if args.counter == "auto" else ""),
                        "slices_per_stream": slices_per_stream},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "what": "device time from the start of a close to its report in host memory"},
             "pairs": pairs_done, "wall_s": wall, "closes": len(lat), "admission_deferrals": deferred,
-            "max_streams_open": max_open}
+            "max_streams_open": max_open,
+            "learned_inference_in_close": bool(args.serve_learned)}
     print(json.dumps(line), flush=True)
 
 
@@ -652,9 +670,10 @@ def scan_alg_bytes(w, pool_info: dict, counter: str) -> float:
     for aging counters."""
     pool_bytes = 4.0 * pool_info["pool_words"]
     if counter == "hist":
-        # the k' latest slice counts of every ATV (2 bytes each); the refresh
-        # runs in its own kernel after the restore
-        return 2.0 * w.k * w.r * pool_info["E"]
+        # the k' latest slice counts of every ATV (2 bytes each) and the
+        # opening phase's count zeroed (2 bytes); the refresh of the two
+        # checked blocks, fused into the same kernel, reads their words
+        return 2.0 * (w.k + 1) * w.r * pool_info["E"] + pool_bytes * 2.0 / (2 * w.k)
     if counter == "ace":
         return 2 * pool_bytes
     if counter == "aligned":
@@ -672,6 +691,24 @@ def roofline_entry(kernel: str, alg_bytes: float, t_s: float, peak: float, peak_
             "ms_per_launch": 1e3 * t_s, "model": model}
 
 
+def auto_counter(k: int, g: int, r: int, E_log2: int) -> str:
+    """Timestamps with slice counts for a pool larger than the L2 cache (the
+    close then reads 2 bytes per ATV and slice instead of the pool), plain
+    timestamps for one that fits (its ingest would pay the slice counts'
+    atomics for a close that is already fast)."""
+    w = max(1, (2 * k).bit_length())          # ceil(log2(2k + 1))
+    w = 8 if w == 7 else w
+    words = -(-(-(-g // (32 // w))) // 8) * 8
+    return "hist" if 4 * r * (1 << E_log2) * words > (128 << 20) else "at"
+
+
+def counter_for(args, w) -> str:
+    """The counter kind of a workload: --counter, or auto_counter's choice."""
+    if args.counter != "auto":
+        return args.counter
+    return auto_counter(w.k, w.g, w.r, w.E_log2)
+
+
 def bench_workload(w, args, world, rank, stream, torch, asse, dist, with_e2e=True):
     """One workload: ingest + fused close per step, device-timed over
     args.steps steps with inputs resident in HBM, then end to end from pinned
@@ -681,7 +718,9 @@ def bench_workload(w, args, world, rank, stream, torch, asse, dist, with_e2e=Tru
     dev = [torch.from_numpy(p.view(np.int32)).cuda() for p in host]
     pinned = [torch.from_numpy(p.view(np.int32)).pin_memory() for p in host] if with_e2e else None
     n_pairs = [p.shape[0] for p in host]
-    pool = asse.Pool(w.params, counter=args.counter, stream=stream.cuda_stream, key_table=args.key_table)
+    counter = counter_for(args, w)
+    pool = asse.Pool(w.params, counter=counter, stream=stream.cuda_stream, key_table=args.key_table,
+                     cluster=args.cluster)
 
     for i in range(args.warmup):
         pool.ingest(dev[i % n_cycled])
@@ -784,12 +823,15 @@ def summarize(w, args, m) -> dict:
     used = m["used"]
     peak, peak_src = peaks()
     alg_ing = statistics.mean(8 * m["n_pairs"][j] + 32 * w.r * m["n_distinct"][j] for j in used)
-    alg_scan = scan_alg_bytes(w, m["info"], args.counter)
+    counter = counter_for(args, w)
+    alg_scan = scan_alg_bytes(w, m["info"], counter)
     r_ing = roofline_entry("ingest", alg_ing, ing, peak, peak_src,
-                           "8 B per pair + 32 B x r per distinct (aip, bip) pair", w.name, args.counter)
+                           "8 B per pair + 32 B x r per distinct (aip, bip) pair", w.name, counter)
     r_ing["distinct_pair_fraction"] = statistics.mean(m["n_distinct"][j] / m["n_pairs"][j] for j in used)
-    r_scan = roofline_entry("scan", alg_scan, scan, peak, peak_src,
-                            "the pool read once + the refreshed words written (Algorithm 2)", w.name, args.counter)
+    r_scan = roofline_entry("hist_scan" if counter == "hist" else "scan", alg_scan, scan, peak, peak_src,
+                            "the k' latest slice counts of every ATV and the opening phase's (2 B each) + the "
+                            "words of the two refreshed blocks" if counter == "hist" else
+                            "the pool read once + the refreshed words written (Algorithm 2)", w.name, counter)
     lat_ms = sorted(1e3 * x for x in m["lat"])
     sector = m["sector"]
     return {
@@ -833,6 +875,8 @@ def main():
     ap.add_argument("--acc-slices", type=int, default=0, help="accuracy mode: slices to run (0: 3k, or k+3 for the "
                                                               "long workload)")
     ap.add_argument("--serve-slices", type=int, default=12)
+    ap.add_argument("--serve-learned", action="store_true",
+                    help="serve mode: run learned per-ATV inference inside every close graph")
     ap.add_argument("--no-accuracy", action="store_true", help="learned mode: skip the training and accuracy leg")
     ap.add_argument("--cycled", type=int, default=0,
                     help="distinct input slices cycled through (0: 8, or 4 for slices over 8 Mi pairs)")
@@ -840,10 +884,14 @@ def main():
                     help="the ingest's slice-wide key table (auto: for pools larger than L2)")
     ap.add_argument("--clocks-dir", default="", help="where the nvidia-smi clock samples of the timed region go "
                                                       "(default: the temporary directory)")
-    ap.add_argument("--counter", default="at", choices=["at", "ace", "aligned", "hist"],
+    ap.add_argument("--counter", default="auto", choices=["auto", "at", "ace", "aligned", "hist"],
                     help="at: the paper's asynchronous timestamps; ace: aging counters; aligned: timestamps with "
                          "one ACT per ATV (whole-pool refresh every k slices); hist: timestamps with per-ATV slice "
-                         "counts kept by the ingest (the close reads the counts)")
+                         "counts kept by the ingest (the close reads the counts); auto: hist for a pool larger "
+                         "than L2, else at")
+    ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="CTAs of a thread-block cluster sharing the ingest's table of seen keys (0: the library's "
+                         "choice)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -896,7 +944,8 @@ def main():
         if world > 1:
             el2, ee2, pd2, ep2 = reduce_over_ranks([el2, ee2], [pd2, ep2], "cuda")
         second = dict(summarize(w2, args, m2), value=pd2 / el2, unit="pkts/s",
-                      ms_per_step=1e3 * el2 / args.steps, config=workload_desc(w2),
+                      ms_per_step=1e3 * el2 / args.steps,
+                      config=dict(workload_desc(w2), counter=counter_for(args, w2).upper()),
                       e2e={"value": ep2 / ee2, "unit": "pkts/s",
                            "h2d_bytes_per_step": int(8 * statistics.mean(m2["n_pairs"])),
                            "d2h_bytes_per_step": int(m2["d2h"] / args.steps)})
@@ -910,7 +959,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(workload_desc(w), counter=args.counter.upper(), key_table=args.key_table,
+            "config": dict(workload_desc(w), counter=counter_for(args, w).upper(), key_table=args.key_table,
+                           cluster=args.cluster,
                            parallelism="replicas" if world > 1 else "single",
                            l2="inputs cycle over %d distinct slices (%d MB) held in HBM, more than L2; the pool "
                               "state stays resident across steps" % (m["n_cycled"],
@@ -932,7 +982,7 @@ def main():
             line[w2.name] = second
         if not args.no_cpu_baseline and world == 1:
             p0 = m["host"][0]
-            dt, cores, text, _ = oracle_slice_time(w, p0, args.counter)
+            dt, cores, text, _ = oracle_slice_time(w, p0, counter_for(args, w))
             line["cpu_baseline"] = {"value": p0.shape[0] / dt, "unit": "pkts/s", "cores": cores, "kind": "oracle",
                                     "sample": text}
         print(json.dumps(line), flush=True)

@@ -110,7 +110,14 @@ extern "C" {
  *          keeps one when the pool is larger than the device's L2 cache (the
  *          repeats then cost DRAM sectors); with the pool in L2 a pool word
  *          costs what a table entry costs.  Results are the same either way.
- *  pad     must be 0.
+ *  cluster CTAs of a thread-block cluster that share one table of the keys
+ *          their ingest has seen (each CTA's shared-memory table holds the
+ *          keys that hash to it, reached by the others through distributed
+ *          shared memory), so that a key repeated across those SMs is set
+ *          once: ASSE_CLUSTER_AUTO (0, no sharing), or 1 (no sharing), 2, 4
+ *          or 8.  Results are the same either way; on a GB300 the remote
+ *          lookup of every pair costs more than the repeats it removes, so
+ *          AUTO does not share.
  */
 typedef struct asse_config {
     uint32_t k, theta, g, r, c, u, s, A;
@@ -119,8 +126,11 @@ typedef struct asse_config {
     uint32_t restore_cap;
     uint64_t max_batch;
     uint32_t key_table;
-    uint32_t pad;
+    uint32_t cluster;
 } asse_config;
+
+/* Value of asse_config.cluster that lets the library choose. */
+#define ASSE_CLUSTER_AUTO 0
 
 /* Values of asse_config.key_table. */
 #define ASSE_KEYS_AUTO 0

@@ -28,7 +28,7 @@ u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_voi
 class Config(ctypes.Structure):
     _fields_ = [("k", u32), ("theta", u32), ("g", u32), ("r", u32), ("c", u32), ("u", u32), ("s", u32),
                 ("A", u32), ("bh_a", u64), ("bh_b", u64), ("counter", u32), ("restore_cap", u32),
-                ("max_batch", u64), ("key_table", u32), ("pad", u32)]
+                ("max_batch", u64), ("key_table", u32), ("cluster", u32)]
 
 
 class SuperPoint(ctypes.Structure):
@@ -158,10 +158,10 @@ def _pairs_arg(pairs):
 
 
 def make_config(params: dict, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
-                key_table: str = "auto") -> Config:
+                key_table: str = "auto", cluster: int = 0) -> Config:
     return Config(int(params["k"]), int(params["theta"]), int(params["g"]), int(params["r"]), int(params["c"]),
                   int(params["u"]), int(params["s"]), int(params["A"]), int(params["bh_a"]), int(params["bh_b"]),
-                  COUNTERS[counter], int(restore_cap), int(max_batch), KEY_TABLE[key_table], 0)
+                  COUNTERS[counter], int(restore_cap), int(max_batch), KEY_TABLE[key_table], int(cluster))
 
 
 class Server:
@@ -265,8 +265,8 @@ class Pool:
     """One ATV cube in device memory (include/asse.h)."""
 
     def __init__(self, params: dict, *, counter: str = "at", restore_cap: int = 0, max_batch: int = 0,
-                 stream: int | None = None, key_table: str = "auto"):
-        cfg = make_config(params, counter, restore_cap, max_batch, key_table)
+                 stream: int | None = None, key_table: str = "auto", cluster: int = 0):
+        cfg = make_config(params, counter, restore_cap, max_batch, key_table, cluster)
         self.cfg = cfg
         self._h = vp()
         self._stream = _current_stream() if stream is None else stream

@@ -149,8 +149,10 @@ int validate(const asse_config *c, std::string &why)
         return bad("bh_a must be odd");
     if (c->theta < 1)
         return bad("theta must be >= 1");
-    if (c->key_table > ASSE_KEYS_OFF || c->pad != 0)
-        return bad("key_table must be ASSE_KEYS_AUTO, ASSE_KEYS_ON or ASSE_KEYS_OFF, and pad 0");
+    if (c->key_table > ASSE_KEYS_OFF)
+        return bad("key_table must be ASSE_KEYS_AUTO, ASSE_KEYS_ON or ASSE_KEYS_OFF");
+    if (c->cluster != ASSE_CLUSTER_AUTO && c->cluster != 1 && c->cluster != 2 && c->cluster != 4 && c->cluster != 8)
+        return bad("cluster must be ASSE_CLUSTER_AUTO, 1, 2, 4 or 8");
     // the scan holds one ATV in a warp tile of at most 512 words
     const uint32_t w = packed_width(c->counter, c->k);
     if ((c->g + 32 / w - 1) / (32 / w) > 512)
@@ -522,6 +524,7 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     P.Ainv = inverse_mod(cfg->A, 4294967311ull);
     P.bh_a = cfg->bh_a;
     P.bh_b = cfg->bh_b;
+    P.cl = cfg->cluster == ASSE_CLUSTER_AUTO ? 1u : cfg->cluster;
     for (uint32_t i = 0; i < 8; i++)
         P.xshift[i] = i < cfg->r ? 2 * P.W - cfg->c - cfg->s * i : 0;
     p->cap = cfg->restore_cap ? cfg->restore_cap : 4096;

@@ -21,6 +21,7 @@
 // the rest of the SM's 256 KB of L1 / shared memory stays L1 cache, which
 // serves the pool words of keys the table missed (a 128 KB table ran 13 %
 // slower, a 192 KB one 2x slower).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -77,15 +78,35 @@ __device__ __forceinline__ uint32_t seen_slot(uint32_t aip, uint32_t h)
     return (aip * 0x9E3779B1u ^ h * 0x85EBCA77u) >> (32 - SEEN_LOG2);
 }
 
-// True if (aip, h) was recorded in this block's table; records it otherwise.
+// True if (aip, h) was recorded in the table of seen keys; records it
+// otherwise.  CL = 1: the block's own table.  CL > 1: the CTAs of a
+// thread-block cluster share one table of CL x 8,192 keys, each CTA holding
+// the keys whose hash picks it, reached by the others through distributed
+// shared memory; a key repeated across the cluster's SMs is then set once.
+// Plain loads and stores: two CTAs that both miss a key set it twice, which
+// only repeats an idempotent SetAT.
+template <int CL>
 __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t aip, uint32_t h)
 {
     const unsigned long long key = ((unsigned long long)aip << 32) | h;
-    const uint32_t s = seen_slot(aip, h);
-    if (seen[s] == key)
-        return true;
-    seen[s] = key;
-    return false;
+    if constexpr (CL == 1) {
+        const uint32_t s = seen_slot(aip, h);
+        if (seen[s] == key)
+            return true;
+        seen[s] = key;
+        return false;
+    } else {
+        constexpr uint32_t CL_LOG2 = CL == 2 ? 1 : (CL == 4 ? 2 : 3);
+        const uint32_t s_all = (aip * 0x9E3779B1u ^ h * 0x85EBCA77u) >> (32 - SEEN_LOG2 - CL_LOG2);
+        const uint32_t owner = s_all >> SEEN_LOG2, s = s_all & ((1u << SEEN_LOG2) - 1);
+        namespace cg = cooperative_groups;
+        cg::cluster_group cluster = cg::this_cluster();
+        unsigned long long *t = owner == cluster.block_rank() ? seen : cluster.map_shared_rank(seen, owner);
+        if (t[s] == key)
+            return true;
+        t[s] = key;
+        return false;
+    }
 }
 
 // True if this lane is the first of the slice to claim key (aip, h) in the
@@ -203,7 +224,7 @@ __device__ __forceinline__ void claim_and_set(const Params &P, uint32_t *pool, u
     set_key<WB, R, HIST>(P, pool, c0, r, e.x, e.y, run);
 }
 
-template <int WB, int R, bool HIST>
+template <int WB, int R, bool HIST, int CL>
 __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     ingest_kernel(Params P, uint32_t *pool, const uint32_t *__restrict__ pairs_raw, uint64_t n_arg,
                   const unsigned long long *n_dev, const SliceCtl *ctl)
@@ -221,7 +242,11 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
     uint2 *q2 = queue + QCAP;
     for (uint32_t i = threadIdx.x; i < (1u << SEEN_LOG2); i += blockDim.x)
         seen[i] = NO_KEY;
-    __syncthreads();
+    // every table of the cluster is empty before any CTA reaches into another's
+    if constexpr (CL > 1)
+        cooperative_groups::this_cluster().sync();
+    else
+        __syncthreads();
     const int r = R ? R : (int)P.r;
     // Warp-uniform loop: the 32 lanes of a warp take 32 consecutive vectors.
     // Keys the block's table has not seen go to the warp's queue; whenever it
@@ -243,8 +268,8 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
         if (v < nvec) {
             h0 = bip_hash(P, cur.y);
             h1 = bip_hash(P, cur.w);
-            do0 = !seen_before(seen, cur.x, h0);
-            do1 = !seen_before(seen, cur.z, h1);
+            do0 = !seen_before<CL>(seen, cur.x, h0);
+            do1 = !seen_before<CL>(seen, cur.z, h1);
         }
         const unsigned m0 = __ballot_sync(FULL_MASK, do0), m1 = __ballot_sync(FULL_MASK, do1);
         if (do0)
@@ -276,6 +301,9 @@ __global__ void __launch_bounds__(INGEST_THREADS, INGEST_BLOCKS_PER_SM)
         const uint2 pr1 = *tail;
         set_key<WB, R, HIST>(P, pool, c0, r, pr1.x, bip_hash(P, pr1.y), true);
     }
+    // no CTA leaves while another may still read its table
+    if constexpr (CL > 1)
+        cooperative_groups::this_cluster().sync();
 }
 
 }  // namespace
@@ -292,18 +320,47 @@ cudaError_t launch_ingest(const Params &P, uint32_t w, uint32_t *pool, const uin
                         (size_t)INGEST_WARPS * (QCAP + (P.keys ? Q2CAP : 0)) * sizeof(uint2);
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        auto kern = P.hist ? (P.r == 4 ? ingest_kernel<WB, 4, true> : ingest_kernel<WB, 0, true>)
-                           : (P.r == 4 ? ingest_kernel<WB, 4, false> : ingest_kernel<WB, 0, false>);
+        auto pick = [&](auto cl) {
+            constexpr int CL = decltype(cl)::value;
+            return P.hist ? (P.r == 4 ? ingest_kernel<WB, 4, true, CL> : ingest_kernel<WB, 0, true, CL>)
+                          : (P.r == 4 ? ingest_kernel<WB, 4, false, CL> : ingest_kernel<WB, 0, false, CL>);
+        };
+        auto kern = P.cl == 8   ? pick(std::integral_constant<int, 8>())
+                    : P.cl == 4 ? pick(std::integral_constant<int, 4>())
+                    : P.cl == 2 ? pick(std::integral_constant<int, 2>())
+                                : pick(std::integral_constant<int, 1>());
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        const int occ = resident_blocks(kern, INGEST_THREADS, smem);
         const uint64_t want = (nvec + INGEST_THREADS - 1) / INGEST_THREADS;
-        const uint64_t full = (uint64_t)sms * occ;
+        cudaLaunchConfig_t lc{};
+        cudaLaunchAttribute attr[1];
+        lc.blockDim = dim3(INGEST_THREADS);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        uint64_t full;
+        if (P.cl > 1) {
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = P.cl;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            // as many whole clusters as are resident at once
+            lc.gridDim = dim3(P.cl);
+            int nc = 0;
+            e = cudaOccupancyMaxActiveClusters(&nc, kern, &lc);
+            if (e != cudaSuccess || nc < 1)
+                return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+            full = (uint64_t)nc * P.cl;
+        } else {
+            full = (uint64_t)sms * resident_blocks(kern, INGEST_THREADS, smem);
+        }
         // with the count only known on the device, the full resident grid
-        const unsigned grid = (unsigned)(n_dev ? full : (want < 1 ? 1 : (want < full ? want : full)));
-        kern<<<grid, INGEST_THREADS, smem, s>>>(P, pool, pairs, n, n_dev, ctl);
-        return cudaGetLastError();
+        uint64_t grid = n_dev ? full : (want < 1 ? 1 : (want < full ? want : full));
+        grid = (grid + P.cl - 1) / P.cl * P.cl;
+        lc.gridDim = dim3((unsigned)grid);
+        return cudaLaunchKernelEx(&lc, kern, P, pool, pairs, n, n_dev, ctl);
     });
 }
 

@@ -39,6 +39,8 @@ struct Params {
     // ASSE_COUNTER_AT_HIST: per ATV, the ATs last set in each slice phase
     // t mod 2k, phase-major ([2k][r * E] 16-bit counts); null otherwise.
     uint16_t *hist;
+    // CTAs of a thread-block cluster sharing the ingest's table of seen keys (1, 2, 4, 8)
+    uint32_t cl;
 };
 
 // Add delta to the 16-bit count hist[i] (a 32-bit atomic on the word that

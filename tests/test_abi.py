@@ -44,7 +44,7 @@ def test_struct_sizes_match_header(lib):
 def _cfg(**kw):
     from paper_1807_01527_gb300 import asse
     base = dict(k=10, theta=1024, g=512, r=4, c=12, u=4, s=6, A=123456789, bh_a=0x9E3779B97F4A7C15, bh_b=7,
-                counter=0, restore_cap=0, max_batch=0, key_table=0, pad=0)
+                counter=0, restore_cap=0, max_batch=0, key_table=0, cluster=0)
     base.update(kw)
     return asse.Config(*[base[f] for f, _ in asse.Config._fields_])
 
@@ -54,7 +54,7 @@ def _cfg(**kw):
     (dict(r=1), "r must"), (dict(r=9), "r must"), (dict(c=17), "c <= 16"), (dict(u=9), "u <= 8"),
     (dict(s=0), "s <= c"), (dict(s=13), "s <= c"), (dict(s=3), "completeness"), (dict(A=1), "A must"),
     (dict(bh_a=2), "odd"), (dict(counter=4), "counter"), (dict(theta=0), "theta"),
-    (dict(key_table=3), "key_table"), (dict(pad=1), "key_table"),
+    (dict(key_table=3), "key_table"), (dict(cluster=3), "cluster"), (dict(cluster=16), "cluster"),
     (dict(c=12, u=4, s=10), "s*(r-1) < 32-u"), (dict(k=100, g=4000), "512 words"),
 ])
 def test_invalid_configs_rejected_without_gpu(lib, bad, msg):

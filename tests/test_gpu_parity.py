@@ -364,6 +364,48 @@ def test_key_table_repeats_and_slice_wrap(mods):
         pl.close()
 
 
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_cluster_shared_seen_table(mods, cluster):
+    """The ingest whose table of seen keys is shared by the CTAs of a
+    thread-block cluster (each CTA holds the keys that hash to it, the others
+    reach it through distributed shared memory) gives the oracle's state,
+    counts and reports: tiny_b for 8 slices, a pool with slice counts and the
+    key table, and the link workload at full size for one slice."""
+    asse, oracle, torch = mods
+    w = synth.workload("tiny_b")
+    pool = asse.Pool(w.params, cluster=cluster)
+    orc = oracle.Oracle.from_params(w.params)
+    for t in range(8):
+        pairs = w.pairs(t)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"tiny_b t={t}")
+        check_close(pool, orc, w.k)
+        orc.advance()
+    pool.close()
+    p = _params(10, 211, 4, 9, 2, 7, 70, seed=cluster)
+    pool = asse.Pool(p, counter="hist", key_table="on", cluster=cluster)
+    orc = oracle.Oracle.from_params(p)
+    for t in range(23):
+        pairs = mixed_pairs(cluster, t, 20001, [35, 70, 140, 280])
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"hist t={t}")
+        check_close(pool, orc, 10 if t % 3 else 4)
+        orc.advance()
+    pool.close()
+    if cluster == 4:
+        wl = synth.workload("link")
+        pool = asse.Pool(wl.params, cluster=cluster)
+        orc = oracle.Oracle.from_params(wl.params)
+        pairs = wl.pairs(0)
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg="link slice 0")
+        check_close(pool, orc, wl.k)
+        pool.close()
+
+
 def test_random_read_probe_leaves_pool_unchanged(mods):
     """The random-read probe (the ingest's random-access roofline) issues at
     least the reads asked for, on the pool's stream, and changes nothing."""
