@@ -109,6 +109,34 @@ __device__ __forceinline__ bool seen_before(unsigned long long *seen, uint32_t a
     }
 }
 
+// L2 accesses to the key table carry the evict-last priority: the pool words
+// and the pair stream that pass through L2 during an ingest would otherwise
+// push the table out between two claims of the same key (measured on the
+// 1.07 GB pool: 0.362 against 0.378 ms; the evict-first priority on the pool
+// words instead made it slower, 0.45 ms, as their compare-and-swap follows
+// the read).
+__device__ __forceinline__ uint64_t l2_evict_last_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ unsigned long long ld_l2_hint(const unsigned long long *a, uint64_t pol)
+{
+    unsigned long long v;
+    asm volatile("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long exch_l2_hint(unsigned long long *a, unsigned long long x, uint64_t pol)
+{
+    unsigned long long v;
+    asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;" : "=l"(v) : "l"(a), "l"(x), "l"(pol)
+                 : "memory");
+    return v;
+}
+
 // True if this lane is the first of the slice to claim key (aip, h) in the
 // key table shared by all blocks.  A key that another block (or an earlier
 // ingest of the same slice) claimed has had, or will have by the end of this
@@ -123,9 +151,10 @@ __device__ __forceinline__ bool claim_key(const Params &P, uint32_t gen, uint32_
     const uint32_t tb = 48 - P.klg;
     const unsigned long long want = ((unsigned long long)gen << 32) | (x & ((1ull << tb) - 1));
     unsigned long long *slot = P.keys + (x >> tb);
-    if (__ldcg(slot) == want)
+    const uint64_t pol = l2_evict_last_policy();
+    if (ld_l2_hint(slot, pol) == want)
         return false;
-    return atomicExch(slot, want) != want;
+    return exch_l2_hint(slot, want, pol) != want;
 }
 
 // SetAT with slice counts (ASSE_COUNTER_AT_HIST): the field is set with a
