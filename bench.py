@@ -41,9 +41,9 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # as null (the kernel has changed since the capture).
 TRAFFIC = {
     ("long", "hist", "ingest"): (1316104448, "667e49c6155a"),
-    ("long", "hist", "hist_scan"): (405193216, "127a9855ddab"),
-    ("link", "at", "ingest"): (201392640, "3c249aac167e"),
-    ("link", "at", "scan"): (96309760, "4ee67a1c66a0"),
+    ("long", "hist", "hist_scan"): (403547392, "0d8fe2a24772"),
+    ("link", "at", "ingest"): (201216000, "667e49c6155a"),
+    ("link", "at", "scan"): (96427264, "4ee67a1c66a0"),
     ("long", "at", "scan"): (1081580032, "4ee67a1c66a0"),
 }
 KERNEL_SOURCES = {
