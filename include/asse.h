@@ -151,11 +151,18 @@ typedef struct asse_pool_info {
     uint32_t w;          /* bits per packed counter field: ceil(log2(2k+1)) (AT) or ceil(log2(k+1))
                           * (ACE), except 8 where that is 7 (four byte-wide fields per word, as many
                           * as 7-bit fields would give; the top bit of each byte stays 0) */
-    uint32_t fields;     /* counters per 32-bit word: floor(32/w); field j at bits [j*w, j*w+w) */
+    uint32_t fields;     /* counters per 32-bit word: floor(32/w); the counter at position p of an
+                          * ATV is field p % fields, bits [j*w, j*w+w), of its word p / fields */
     uint32_t words;      /* 32-bit words per ATV, ceil(g/fields) rounded up to a multiple of 8 */
     uint32_t E;          /* ATVs per row: 2^(c+u); ATV index in a row = (frame << c) | column */
     uint32_t threshold;  /* super-ATV count threshold ceil(g - g*exp(-theta/g)) (Sec. 4.2) */
-    uint32_t block;      /* ATs per ACT block: floor(g/2k) (g for ASSE_COUNTER_AT_ALIGNED) */
+    uint32_t block;      /* ATs per ACT block: floor(g/2k) (g for ASSE_COUNTER_AT_ALIGNED); block b
+                          * holds ATs [b*block, (b+1)*block) and the last of the 2k blocks the rest of g */
+    uint32_t k;          /* slices per window (cfg k) */
+    uint32_t paired;     /* 1 (ASSE_COUNTER_AT, ASSE_COUNTER_AT_HIST): the 2k blocks are stored in the
+                          * order 0, k, 1, k+1, ..., k-1, 2k-1, so the two blocks one refresh
+                          * (Algorithm 2) checks are adjacent: AT h of block b sits at position
+                          * h - b*block + s*block, s = 2b (b < k) or 2(b-k)+1; 0: AT h at position h */
     uint64_t slice;      /* index of the open slice (0 after create) */
     uint64_t pool_words; /* r * E * words */
     const uint32_t *pool;/* device address of the packed pool, [r][E][words] */

@@ -37,7 +37,7 @@ class SuperPoint(ctypes.Structure):
 
 class PoolInfo(ctypes.Structure):
     _fields_ = [("w", u32), ("fields", u32), ("words", u32), ("E", u32), ("threshold", u32), ("block", u32),
-                ("slice", u64), ("pool_words", u64), ("pool", vp)]
+                ("k", u32), ("paired", u32), ("slice", u64), ("pool_words", u64), ("pool", vp)]
 
 
 class SynthCfg(ctypes.Structure):

@@ -521,6 +521,9 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     P.blk = p->blk;
     P.F = p->F;
     P.blk_magic = ((1ull << 32) + p->blk - 1) / p->blk;
+    // timestamps with 2k blocks keep each pair of blocks that one refresh
+    // checks side by side (block_slot)
+    P.paired = (cfg->counter == ASSE_COUNTER_AT || cfg->counter == ASSE_COUNTER_AT_HIST) ? 1 : 0;
     P.Ainv = inverse_mod(cfg->A, 4294967311ull);
     P.bh_a = cfg->bh_a;
     P.bh_b = cfg->bh_b;
@@ -928,6 +931,8 @@ int asse_info(const asse_pool *p, asse_pool_info *out)
     out->E = 1u << p->P.E_log2;
     out->threshold = p->P.T;
     out->block = p->blk;
+    out->k = p->P.k;
+    out->paired = p->P.paired;
     out->slice = p->t;
     out->pool_words = p->pool_words;
     out->pool = p->pool;

@@ -94,6 +94,32 @@ __device__ __forceinline__ uint32_t act_block(const Params &P, uint32_t h)
     return b < P.k2 - 1 ? b : P.k2 - 1;
 }
 
+// ACT block of the AT stored at position p of an ATV (block_slot order when
+// P.paired).
+__device__ __forceinline__ uint32_t pos_block(const Params &P, uint32_t p)
+{
+    const uint32_t s = act_block(P, p);
+    return P.paired ? slot_block(P.k, s) : s;
+}
+
+// Storage position of AT h (h itself unless P.paired).
+__device__ __forceinline__ uint32_t at_pos(const Params &P, uint32_t h)
+{
+    if (!P.paired)
+        return h;
+    const uint32_t b = act_block(P, h);
+    return h - b * P.blk + block_slot(P.k, b) * P.blk;
+}
+
+// The AT stored at position p (the inverse of at_pos).
+__device__ __forceinline__ uint32_t pos_at(const Params &P, uint32_t p)
+{
+    if (!P.paired)
+        return p;
+    const uint32_t s = act_block(P, p);
+    return p - s * P.blk + slot_block(P.k, s) * P.blk;
+}
+
 // ACT of block b in the slice whose block 0 has ACT c0.
 __device__ __forceinline__ uint32_t act_of(const Params &P, uint32_t c0, uint32_t b)
 {
@@ -140,7 +166,7 @@ __device__ __forceinline__ uint32_t active_fields(const Params &P, uint32_t word
             am |= (uint32_t)(v + kp >= P.k + 1) << j;
         }
     } else {
-        const uint32_t b0 = act_block(P, h0), b1 = act_block(P, h0 + F - 1);
+        const uint32_t b0 = pos_block(P, h0), b1 = pos_block(P, h0 + F - 1);
         if (b0 == b1) {
             // one ACT for the whole word: active values are the cyclic window
             // act, act-1, ..., act-k'+1 (mod 2k)
@@ -156,7 +182,7 @@ __device__ __forceinline__ uint32_t active_fields(const Params &P, uint32_t word
 #pragma unroll 1
             for (int j = 0; j < F; j++) {
                 const uint32_t v = (word >> (j * WB)) & FM;
-                am |= (uint32_t)field_active(P, v, act_of(P, c0, act_block(P, h0 + j)), kp) << j;
+                am |= (uint32_t)field_active(P, v, act_of(P, c0, pos_block(P, h0 + j)), kp) << j;
             }
         }
     }

@@ -53,7 +53,7 @@ __device__ void feature_tables(const Params &P, uint32_t c0, uint32_t kp, RangeD
         for (uint32_t j = 0; j < F; j++) {
             const uint32_t h = q * F + j;
             if (h < P.g)
-                a |= act_of(P, c0, act_block(P, h)) << (j * WB);
+                a |= act_of(P, c0, pos_block(P, h)) << (j * WB);
         }
         actw[q] = a;
     }

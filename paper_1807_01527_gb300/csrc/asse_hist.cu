@@ -54,13 +54,16 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint3
     }
     __syncthreads();
     uint32_t *my_mask = maskbuf + warp * P.mw;
-    // the refreshed words as up to four (range, offset) slots when each of
-    // the (at most two) ranges spans at most two words
+    // the refreshed words as up to four slots when the (at most two) ranges
+    // hold at most four words together
     const uint32_t n0 = R.n_ranges > 0 ? R.q_hi[0] - R.q_lo[0] + 1 : 0;
     const uint32_t n1 = R.n_ranges > 1 ? R.q_hi[1] - R.q_lo[1] + 1 : 0;
-    const bool short_ranges = n0 <= 2 && n1 <= 2;
-    const uint32_t rq[4] = {R.q_lo[0], R.q_lo[0] + 1, R.q_lo[1], R.q_lo[1] + 1};
-    const uint32_t rmask = (n0 > 0 ? 1u : 0u) | (n0 > 1 ? 2u : 0u) | (n1 > 0 ? 4u : 0u) | (n1 > 1 ? 8u : 0u);
+    const bool short_ranges = n0 + n1 <= 4;
+    uint32_t rq[4];
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++)
+        rq[j] = j < n0 ? R.q_lo[0] + j : R.q_lo[1] + (j - n0);
+    const uint32_t rmask = (1u << (short_ranges ? n0 + n1 : 0u)) - 1u;
     const uint32_t cols = P.cmask + 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * V;
     for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + warp * 32u) * V; base < total_atv; base += stride) {
@@ -153,9 +156,10 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint3
         if (FUSE && mine) {
             // Algorithm 2 for the next slice on the words of the two checked
             // blocks of each ATV, and the counts of the opening phase zeroed.
-            // Ranges of at most two words each (every block but a long last
-            // one): the words of all V ATVs are loaded before any is
-            // written back, so the thread has them in flight together.
+            // At most four words (two blocks of up to eight byte-wide fields,
+            // every pair but the one with the long last block): the words of
+            // RG ATVs are loaded before any is written back, so the thread
+            // has them in flight together.
             if (short_ranges) {
                 constexpr int G = V < RG ? V : RG;
 #pragma unroll 1
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_rebuild_kernel(Params P, co
                 const uint32_t v = (word >> (j * WB)) & FM;
                 if (h >= P.g || v >= P.k2)
                     continue;
-                uint32_t age = act_of(P, c0, act_block(P, h)) + P.k2 - v;
+                uint32_t age = act_of(P, c0, pos_block(P, h)) + P.k2 - v;
                 age = age >= P.k2 ? age - P.k2 : age;
                 if (age < P.k) {
                     const uint32_t ph = c0 >= age ? c0 - age : c0 + P.k2 - age;

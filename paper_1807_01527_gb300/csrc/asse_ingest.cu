@@ -204,8 +204,9 @@ __device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_
     uint32_t z;
     prep_host(P, aip, LL, z);
     const uint32_t val = P.ace ? P.k : act_of(P, c0, act_block(P, h));
-    const uint32_t q = h / F;
-    const uint32_t sh = (h - q * F) * WB;
+    const uint32_t pos = at_pos(P, h);  // where AT h is stored in its ATV
+    const uint32_t q = pos / F;
+    const uint32_t sh = (pos - q * F) * WB;
     uint32_t *a[RM];
     uint32_t o[RM];
 #pragma unroll

@@ -41,7 +41,26 @@ struct Params {
     uint16_t *hist;
     // CTAs of a thread-block cluster sharing the ingest's table of seen keys (1, 2, 4, 8)
     uint32_t cl;
+    // 1: the 2k ACT blocks of an ATV are stored in pairs (block_slot below);
+    // 0: AT h at position h (aging counters, the aligned variant)
+    uint32_t paired;
 };
+
+// Storage order of the ACT blocks of a timestamp ATV with 2k blocks: block b
+// and block b + k, which Algorithm 2 checks in the same slice (their ACTs
+// differ by k), sit side by side: 0, k, 1, k + 1, ..., k - 1, 2k - 1.  Every
+// block but the last holds blk ATs and the last (2k - 1) also comes last, so
+// slot s starts at position s * blk.  A refresh then touches one stretch of
+// each ATV instead of two stretches k blocks apart.
+__host__ __device__ inline uint32_t block_slot(uint32_t k, uint32_t b)
+{
+    return b < k ? 2 * b : 2 * (b - k) + 1;
+}
+
+__host__ __device__ inline uint32_t slot_block(uint32_t k, uint32_t s)
+{
+    return (s & 1) ? k + (s >> 1) : s >> 1;
+}
 
 // Add delta to the 16-bit count hist[i] (a 32-bit atomic on the word that
 // holds it; a count stays in 0..g, so its neighbour never sees a carry).
@@ -158,11 +177,13 @@ struct SliceCtl {
 };
 
 // Words holding the ACT blocks whose ACT becomes 0 or k when slice t_new
-// opens.  Blocks are contiguous: the first 2k-1 of blk ATs, the last the rest
-// of g.  blk == g is the aligned variant: the ATV is one block with ACT C0,
-// which reaches 0 or k once every k slices (no range in between).
+// opens.  Blocks are contiguous runs of ATs: the first 2k-1 of blk ATs, the
+// last the rest of g; paired: stored in the order of block_slot, which puts
+// the two blocks side by side (one range).  blk == g is the aligned variant:
+// the ATV is one block with ACT C0, which reaches 0 or k once every k slices
+// (no range in between).
 __host__ __device__ inline Refresh refresh_for(uint32_t k, uint32_t g, uint32_t blk, uint32_t F,
-                                               unsigned long long t_new)
+                                               unsigned long long t_new, bool paired)
 {
     const uint32_t k2 = 2 * k;
     const uint32_t nblk = blk >= g ? 1 : k2;
@@ -173,7 +194,8 @@ __host__ __device__ inline Refresh refresh_for(uint32_t k, uint32_t g, uint32_t 
     for (int i = 0; i < 2; i++) {
         if (b[i] >= nblk)
             continue;
-        const uint32_t flo = b[i] * blk, fhi = b[i] == nblk - 1 ? g : (b[i] + 1) * blk;
+        const uint32_t sl = paired ? block_slot(k, b[i]) : b[i];
+        const uint32_t flo = sl * blk, fhi = sl == nblk - 1 ? g : (sl + 1) * blk;
         lo[n] = flo / F;
         hi[n] = (fhi - 1) / F;
         n++;
@@ -210,7 +232,7 @@ __host__ __device__ inline SliceCtl slice_ctl(const Params &P, unsigned long lon
     SliceCtl c{};
     c.t = t;
     c.c0 = (uint32_t)(t % P.k2);
-    c.R = refresh_for(P.k, P.g, P.blk, P.F, t + 1);
+    c.R = refresh_for(P.k, P.g, P.blk, P.F, t + 1, P.paired != 0);
     return c;
 }
 

@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(256) synth_kernel(Params P, SynthArgs S, uint6
         for (uint32_t q = tid; q < P.Wd; q += blockDim.x) {
             uint32_t wd = 0;
             for (uint32_t j = 0; j < F; j++) {
-                const uint32_t h = q * F + j;
-                if (h < P.g) {
+                const uint32_t pos = q * F + j;
+                if (pos < P.g) {
+                    const uint32_t h = pos_at(P, pos);  // the AT stored there
                     const int s = last[h];
                     const uint32_t v = s < 0 ? P.k2 : act_of(P, (uint32_t)s, act_block(P, h));
                     wd |= v << (j * WB);
@@ -456,6 +457,7 @@ int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uin
     P.r = cfg->r;
     P.blk = cfg->g / (2 * cfg->k);
     P.blk_magic = ((1ull << 32) + P.blk - 1) / P.blk;
+    P.paired = 1;  // the storage order of a timestamp pool's ACT blocks
     P.bh_a = cfg->bh_a;
     P.bh_b = cfg->bh_b;
     const uint32_t w = packed_width(ASSE_COUNTER_AT, cfg->k);

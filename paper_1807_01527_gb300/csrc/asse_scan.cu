@@ -348,7 +348,7 @@ __device__ __forceinline__ uint32_t refresh_word(const Params &P, uint32_t word,
     for (uint32_t j = 0; j < F; j++) {
         const uint32_t h = q * F + j;
         if (h < P.g) {
-            const uint32_t a = act_of(P, c0n, act_block(P, h));
+            const uint32_t a = act_of(P, c0n, pos_block(P, h));
             const uint32_t v = (word >> (j * WB)) & FM;
             out = (out & ~(FM << (j * WB))) | (preserve(P, v, a) << (j * WB));
         }

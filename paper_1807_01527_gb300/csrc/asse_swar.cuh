@@ -90,7 +90,7 @@ __device__ RangeDesc count_desc(const Params &P, uint32_t q, uint32_t c0, uint32
                 l1 = P.k + 1 - kp;
                 h1 = P.k;
             } else {
-                const uint32_t act = act_of(P, c0, act_block(P, h));
+                const uint32_t act = act_of(P, c0, pos_block(P, h));
                 if (act + 1 >= kp) {
                     l1 = act + 1 - kp;
                     h1 = act;
@@ -118,7 +118,7 @@ __device__ RangeDesc refresh_desc(const Params &P, uint32_t q, uint32_t c0n)
         const uint32_t h = q * S::F + j;
         uint32_t l1 = S::FM, h1 = 0, l2 = S::FM, h2 = 0;
         if (h < P.g && !P.ace) {
-            const uint32_t act = act_of(P, c0n, act_block(P, h));
+            const uint32_t act = act_of(P, c0n, pos_block(P, h));
             if (act == 0) {
                 l1 = 0;
                 h1 = P.k;
@@ -216,7 +216,7 @@ __device__ __forceinline__ uint4 count_desc_bytes(const Params &P, uint32_t q, u
                 l1 = P.k + 1 - kp;
                 h1 = P.k;
             } else {
-                const uint32_t act = act_of(P, c0, act_block(P, h));
+                const uint32_t act = act_of(P, c0, pos_block(P, h));
                 if (act + 1 >= kp) {
                     l1 = act + 1 - kp;
                     h1 = act;
@@ -245,7 +245,7 @@ __device__ __forceinline__ uint4 refresh_desc_bytes(const Params &P, uint32_t q,
         const uint32_t h = q * 4 + j;
         uint32_t l1 = 127, h1 = 0, l2 = 127, h2 = 0;
         if (h < P.g && !P.ace) {
-            const uint32_t act = act_of(P, c0n, act_block(P, h));
+            const uint32_t act = act_of(P, c0n, pos_block(P, h));
             if (act == 0) {
                 l1 = 0;
                 h1 = P.k;

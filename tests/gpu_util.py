@@ -107,15 +107,29 @@ def check_close(pool, orc, kp, *, cap_ok=True):
     return res
 
 
+def at_positions(info: dict, g: int) -> np.ndarray:
+    """Storage position of every AT h of an ATV, as asse_info describes it:
+    h itself, or with paired blocks (the 2k ACT blocks stored in the order 0,
+    k, 1, k+1, ...) h - b*block + s*block for h in block b, s its slot."""
+    h = np.arange(g)
+    if not info["paired"]:
+        return h
+    k, blk = info["k"], info["block"]
+    b = np.minimum(h // blk, 2 * k - 1)
+    s = np.where(b < k, 2 * b, 2 * (b - k) + 1)
+    return h - b * blk + s * blk
+
+
 def unpack_pool(words: np.ndarray, info: dict, g: int) -> np.ndarray:
     """Packed pool words [r][E][words] -> counter values [r][E][g] (uint8):
-    field j of a word holds bits [j*w, j*w+w), AT h lives in word h // fields
-    (w and fields as asse_info reports them)."""
+    the counter at position p is field p % fields, bits [j*w, j*w+w), of word
+    p // fields, and AT h sits at position at_positions(h) (w, fields and the
+    block order as asse_info reports them)."""
     w, F = info["w"], info["fields"]
     words = words.reshape(-1, info["E"], info["words"])
-    h = np.arange(g)
-    sel = words[:, :, h // F]
-    return ((sel >> ((h % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
+    pos = at_positions(info, g)
+    sel = words[:, :, pos // F]
+    return ((sel >> ((pos % F) * w).astype(np.uint32)) & ((1 << w) - 1)).astype(np.uint8)
 
 
 def state(pool) -> np.ndarray:

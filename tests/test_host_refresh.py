@@ -3,7 +3,9 @@ each slice (the words holding the ACT blocks that Algorithm 2 checks when a
 slice opens), for the staggered blocks of Sec. 3 and for the aligned variant
 (one block), against a brute force over every AT: the ranges must cover
 every word holding an AT whose new ACT is 0 or k, stay inside the ATV, and
-start and end on such words.  Built with the host compiler, no GPU needed."""
+start and end on such words; with the paired block order of timestamp pools
+(blocks b and b + k side by side) they must form one range.  Built with the
+host compiler, no GPU needed."""
 import os
 import shutil
 import subprocess
@@ -36,20 +38,20 @@ def _cases():
                 continue
             for w in (ww for ww in range(1, 9) if (1 << ww) > 2 * k):
                 F = 32 // w
-                for aligned in (False, True):
+                for aligned, paired in ((False, False), (False, True), (True, False)):
                     blk = g if aligned else g // (2 * k)
                     for t in range(1, 2 * k + 2):
-                        out.append((k, g, blk, F, t, aligned))
+                        out.append((k, g, blk, F, t, int(paired), aligned))
                 break  # the AT width of this k
     return out
 
 
 def test_refresh_ranges_cover_exactly_the_checked_blocks(ranges_tool):
     cases = _cases()
-    inp = "".join("%d %d %d %d %d\n" % c[:5] for c in cases)
+    inp = "".join("%d %d %d %d %d %d\n" % c[:6] for c in cases)
     res = subprocess.run([ranges_tool], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
     assert len([r for r in res if r]) == len(cases)
-    for (k, g, blk, F, t, aligned), line in zip(cases, res):
+    for (k, g, blk, F, t, paired, aligned), line in zip(cases, res):
         c0n, n, lo0, hi0, lo1, hi1 = map(int, line.split())
         k2 = 2 * k
         assert c0n == t % k2
@@ -57,8 +59,10 @@ def test_refresh_ranges_cover_exactly_the_checked_blocks(ranges_tool):
         need = set()
         for h in range(g):
             b = min(h // blk, nblk - 1)
+            # storage position of AT h: paired slots 0, k, 1, k+1, ... (all of blk ATs but the last block)
+            pos = h - b * blk + (2 * b if b < k else 2 * (b - k) + 1) * blk if paired else h
             if (c0n + b) % k2 in (0, k):
-                need.add(h // F)
+                need.add(pos // F)
         ranges = [(lo0, hi0), (lo1, hi1)][:n]
         covered = set()
         for lo, hi in ranges:
@@ -67,6 +71,8 @@ def test_refresh_ranges_cover_exactly_the_checked_blocks(ranges_tool):
             covered |= set(range(lo, hi + 1))
         assert need <= covered, (k, g, aligned, t, sorted(need - covered))
         assert (n == 0) == (not need)
+        if paired:
+            assert n == 1, (k, g, t, ranges)
         if aligned:
             # one block: the whole ATV every k slices, nothing in between
             assert (n == 1) == (t % k == 0)
