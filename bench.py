@@ -40,11 +40,11 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # A figure whose source id no longer matches the current sources is reported
 # as null (the kernel has changed since the capture).
 TRAFFIC = {
-    ("long", "hist", "ingest"): (1316104448, "667e49c6155a"),
-    ("long", "hist", "hist_scan"): (403547392, "0d8fe2a24772"),
-    ("link", "at", "ingest"): (201216000, "667e49c6155a"),
-    ("link", "at", "scan"): (96427264, "4ee67a1c66a0"),
-    ("long", "at", "scan"): (1081580032, "4ee67a1c66a0"),
+    ("long", "hist", "ingest"): (1315014152, "d2db03fbd6a6"),
+    ("long", "hist", "hist_scan"): (147243248, "e75cda0555d3"),
+    ("link", "at", "ingest"): (201394944, "d2db03fbd6a6"),
+    ("link", "at", "scan"): (96553728, "4571ec86596b"),
+    ("long", "at", "scan"): (1081540752, "4571ec86596b"),
 }
 KERNEL_SOURCES = {
     "ingest": ["asse_ingest.cu", "asse_device.cuh", "asse_internal.h"],
@@ -663,7 +663,7 @@ def train_candidate_model(asse, w, stream, torch, bg_max: float, n_max_log2: int
                               "within_10pct_eq4": (rel_e[near] <= 0.1).double().mean().item()}}
 
 
-def scan_alg_bytes(w, pool_info: dict, counter: str) -> float:
+def scan_alg_bytes(w, pool_info: dict, counter: str, kp: int | None = None) -> float:
     """Algorithmic bytes of one fused scan: the pool read once, plus the words
     the refresh rewrites: the two ACT blocks whose ACT becomes 0 or k (2 of
     the 2k blocks of every ATV, Algorithm 2) for timestamps, every word
@@ -671,10 +671,14 @@ def scan_alg_bytes(w, pool_info: dict, counter: str) -> float:
     for aging counters."""
     pool_bytes = 4.0 * pool_info["pool_words"]
     if counter == "hist":
-        # the k' latest slice counts of every ATV (2 bytes each) and the
-        # opening phase's count zeroed (2 bytes); the refresh of the two
-        # checked blocks, fused into the same kernel, reads their words
-        return 2.0 * (w.k + 1) * w.r * pool_info["E"] + pool_bytes * 2.0 / (2 * w.k)
+        # per ATV: its window sum read and written back, the count of the
+        # phase leaving the window read, the opening phase's count zeroed (2
+        # bytes each; a window shorter than k reads its k' counts instead of
+        # the sum); the refresh of the two checked blocks, fused into the same
+        # kernel, reads their words
+        kp = w.k if kp is None else kp
+        per_atv = 8.0 if kp == w.k else 2.0 * kp + 8.0
+        return per_atv * w.r * pool_info["E"] + pool_bytes * 2.0 / (2 * w.k)
     if counter == "ace":
         return 2 * pool_bytes
     if counter == "aligned":
@@ -830,8 +834,8 @@ def summarize(w, args, m) -> dict:
                            "8 B per pair + 32 B x r per distinct (aip, bip) pair", w.name, counter)
     r_ing["distinct_pair_fraction"] = statistics.mean(m["n_distinct"][j] / m["n_pairs"][j] for j in used)
     r_scan = roofline_entry("hist_scan" if counter == "hist" else "scan", alg_scan, scan, peak, peak_src,
-                            "the k' latest slice counts of every ATV and the opening phase's (2 B each) + the "
-                            "words of the two refreshed blocks" if counter == "hist" else
+                            "per ATV its window sum read and written, the leaving and the opening phase's "
+                            "counts (2 B each) + the words of the two refreshed blocks" if counter == "hist" else
                             "the pool read once + the refreshed words written (Algorithm 2)", w.name, counter)
     lat_ms = sorted(1e3 * x for x in m["lat"])
     sector = m["sector"]

@@ -74,7 +74,9 @@ extern "C" {
  * reads AT words only for the super ATVs and the two blocks preserveAT
  * checks.  A count is zeroed when its phase comes round again (every AT it
  * counted has been cleared by then, Algorithm 2), so ATs cleared by the
- * refresh need no update.  Costs 4k bytes per ATV. */
+ * refresh need no update.  A running sum of the k latest counts per ATV
+ * (kept by the ingest and the refresh) answers the full window k' = k with
+ * one read.  Costs 4k + 2 bytes per ATV. */
 #define ASSE_COUNTER_AT_HIST 3
 
 /* Flags of asse_superpoint. */
@@ -85,8 +87,9 @@ extern "C" {
  *  k       window size in slices (1..127); AT values are 0..2k, 2k inactive.
  *  theta   super-point threshold on the cardinality (Sec. 2.1).
  *  g       ATs per ATV, 2k <= g <= 4096 and g <= 512 * floor(32/w) (an ATV
- *          fits in 512 words).  The 2k ACT blocks are contiguous:
- *          the first 2k-1 hold floor(g/2k) ATs each, the last the rest.
+ *          fits in 512 words).  The 2k ACT blocks are contiguous runs of
+ *          AT indices: the first 2k-1 hold floor(g/2k) ATs each, the last
+ *          the rest (their storage order: asse_pool_info.paired).
  *  r       rows, 2..8.
  *  c       column-index bits (ATVs per row and frame = 2^c), 1..16.
  *  u       frame bits (frames = 2^u), 0..8; c + u <= 24.

@@ -279,6 +279,7 @@ void free_all(asse_pool *p)
     cudaFree(p->ctl);
     cudaFree(p->P.keys);
     cudaFree(p->P.hist);
+    cudaFree(p->P.hsum);
     cudaFree(p->stage[0]);
     cudaFree(p->stage[1]);
     cudaFree(p->q_aips);
@@ -431,7 +432,7 @@ uint64_t pool_device_bytes(const asse_config *cfg)
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
         cudaGetLastError();
     const uint32_t klg = key_table_log2(n_atv, n_atv * Wd * 4, (unsigned long long)l2, cfg->key_table);
-    const uint64_t hist = cfg->counter == ASSE_COUNTER_AT_HIST ? (uint64_t)2 * cfg->k * n_atv * 2 : 0;
+    const uint64_t hist = cfg->counter == ASSE_COUNTER_AT_HIST ? ((uint64_t)2 * cfg->k + 1) * n_atv * 2 : 0;
     return hist + n_atv * Wd * 4 + n_atv * 2 + nseg * (8 + 4) + n_atv * 4 + n_atv * mw * 4 + nf * 2 * cap * sizeof(Tuple) +
            2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8 +
            (klg ? sizeof(unsigned long long) << klg : 0);
@@ -566,8 +567,10 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
     P.klg = key_table_log2(n_atv, p->pool_words * 4, (unsigned long long)l2, cfg->key_table);
     if (P.klg)
         alloc((void **)&P.keys, sizeof(unsigned long long) << P.klg);
-    if (cfg->counter == ASSE_COUNTER_AT_HIST)
+    if (cfg->counter == ASSE_COUNTER_AT_HIST) {
         alloc((void **)&P.hist, (size_t)2 * k * n_atv * sizeof(uint16_t));
+        alloc((void **)&P.hsum, (size_t)n_atv * sizeof(uint16_t));
+    }
     alloc((void **)&p->stage[0], p->stage_pairs * 8);
     alloc((void **)&p->stage[1], p->stage_pairs * 8);
     if (e == cudaSuccess)
@@ -611,6 +614,8 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
         e = cudaMemsetAsync(P.keys, 0xff, sizeof(unsigned long long) << P.klg, p->stream);
     if (e == cudaSuccess && P.hist)
         e = cudaMemsetAsync(P.hist, 0, (size_t)2 * k * n_atv * sizeof(uint16_t), p->stream);
+    if (e == cudaSuccess && P.hsum)
+        e = cudaMemsetAsync(P.hsum, 0, (size_t)n_atv * sizeof(uint16_t), p->stream);
     const SliceCtl ctl0 = slice_ctl(P, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, p->stream);

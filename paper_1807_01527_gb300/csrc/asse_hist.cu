@@ -29,13 +29,45 @@ constexpr int HIST_WARPS = HIST_THREADS / 32;
 // time -> 0.080; more registers cost resident warps)
 constexpr int RG = 2;
 
+// V consecutive 16-bit counts from p (V = 8: one 16-byte load).
+template <int V>
+__device__ __forceinline__ void load_counts(const uint16_t *p, uint32_t (&c)[V])
+{
+    if constexpr (V == 8) {
+        const uint4 h = *reinterpret_cast<const uint4 *>(p);
+        c[0] = h.x & 0xffffu;
+        c[1] = h.x >> 16;
+        c[2] = h.y & 0xffffu;
+        c[3] = h.y >> 16;
+        c[4] = h.z & 0xffffu;
+        c[5] = h.z >> 16;
+        c[6] = h.w & 0xffffu;
+        c[7] = h.w >> 16;
+    } else {
+        c[0] = p[0];
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_counts(uint16_t *p, const uint32_t (&c)[V])
+{
+    if constexpr (V == 8)
+        *reinterpret_cast<uint4 *>(p) =
+            make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+    else
+        p[0] = (uint16_t)c[0];
+}
+
 // V ATVs per thread (8: one 16-byte load per phase, the ATVs of one thread
-// in one row-frame; 1 for pools with fewer than 8 columns).  FUSE: the close
-// of a slice, which also runs Algorithm 2 on the two checked blocks of each
-// of the thread's ATVs (after the warp has built the masks of its super
-// ATVs from the unrefreshed words) and zeroes the counts of the opening
-// slice's phase (not a phase of the window being counted).
-template <int WB, bool FUSE, int V>
+// in one row-frame; 1 for pools with fewer than 8 columns).  SUM: the
+// window is the full k slices, whose counts the ATV's running sum holds (one
+// read instead of k).  FUSE: the close of a slice, which also runs Algorithm
+// 2 on the two checked blocks of each of the thread's ATVs (after the warp
+// has built the masks of its super ATVs from the unrefreshed words), takes
+// the phase that is about to leave the window out of the running sums and
+// zeroes the counts of the opening slice's phase (not a phase of the window
+// being counted).
+template <int WB, bool FUSE, int V, bool SUM>
 __global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint32_t *pool, uint32_t kp,
                                                                  const SliceCtl *ctl, ScanOut o, uint32_t total_atv)
 {
@@ -74,31 +106,21 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint3
         for (int v = 0; v < V; v++)
             c[v] = 0;
         if (mine) {
-            // phases c0, c0-1, ..., c0-k'+1 (mod 2k): the slices of the window
-            uint32_t ph = c0;
-            for (uint32_t a = 0; a < kp; a++) {
-                const uint16_t *row = P.hist + (uint64_t)ph * total_atv + a0;
-                if constexpr (V == 8) {
-                    const uint4 h = *reinterpret_cast<const uint4 *>(row);
-                    c[0] += h.x & 0xffffu;
-                    c[1] += h.x >> 16;
-                    c[2] += h.y & 0xffffu;
-                    c[3] += h.y >> 16;
-                    c[4] += h.z & 0xffffu;
-                    c[5] += h.z >> 16;
-                    c[6] += h.w & 0xffffu;
-                    c[7] += h.w >> 16;
-                } else {
-                    c[0] += row[0];
-                }
-                ph = ph == 0 ? P.k2 - 1 : ph - 1;
-            }
-            if constexpr (V == 8) {
-                *reinterpret_cast<uint4 *>(o.cnt + a0) =
-                    make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+            if constexpr (SUM) {
+                load_counts<V>(P.hsum + a0, c);
             } else {
-                o.cnt[a0] = (uint16_t)c[0];
+                // phases c0, c0-1, ..., c0-k'+1 (mod 2k): the slices of the window
+                uint32_t ph = c0;
+                for (uint32_t a = 0; a < kp; a++) {
+                    uint32_t h[V];
+                    load_counts<V>(P.hist + (uint64_t)ph * total_atv + a0, h);
+#pragma unroll
+                    for (int v = 0; v < V; v++)
+                        c[v] += h[v];
+                    ph = ph == 0 ? P.k2 - 1 : ph - 1;
+                }
             }
+            store_counts<V>(o.cnt + a0, c);
         }
         // the V ATVs of a thread share a row-frame (2^c is a multiple of V)
         const uint32_t sg = mine ? (uint32_t)(a0 >> P.c) : 0xffffffffu;  // row * 2^u + frame
@@ -198,18 +220,31 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_scan_kernel(Params P, uint3
                         }
                 }
             }
-            uint16_t *hz = P.hist + (uint64_t)R.c0n * total_atv + a0;
-            if constexpr (V == 8)
-                *reinterpret_cast<uint4 *>(hz) = make_uint4(0, 0, 0, 0);
-            else
-                hz[0] = 0;
+            // the window after this slice loses phase c0 - k + 1 (mod 2k)
+            const uint32_t leave = c0 + P.k + 1 >= P.k2 ? c0 + P.k + 1 - P.k2 : c0 + P.k + 1;
+            uint32_t lc[V], sv[V];
+            load_counts<V>(P.hist + (uint64_t)leave * total_atv + a0, lc);
+            if constexpr (SUM) {
+#pragma unroll
+                for (int v = 0; v < V; v++)
+                    sv[v] = c[v] - lc[v];
+            } else {
+                load_counts<V>(P.hsum + a0, sv);
+#pragma unroll
+                for (int v = 0; v < V; v++)
+                    sv[v] -= lc[v];
+            }
+            store_counts<V>(P.hsum + a0, sv);
+            const uint32_t zero[V] = {};
+            store_counts<V>(P.hist + (uint64_t)R.c0n * total_atv + a0, zero);
         }
     }
 }
 
 // The slice counts of a pool counted from its words (after asse_load): every
 // AT set d < k slices ago, d = (ACT - value) mod 2k, adds one to the count of
-// phase t - d.  Counts of older phases stay zero (no window reads them).
+// phase t - d and to the ATV's window sum.  Counts of older phases stay zero
+// (no window reads them).
 template <int WB>
 __global__ void __launch_bounds__(HIST_THREADS) hist_rebuild_kernel(Params P, const uint32_t *pool, const SliceCtl *ctl,
                                                                     uint32_t total_atv)
@@ -231,6 +266,7 @@ __global__ void __launch_bounds__(HIST_THREADS) hist_rebuild_kernel(Params P, co
                 if (age < P.k) {
                     const uint32_t ph = c0 >= age ? c0 - age : c0 + P.k2 - age;
                     hist_add(P.hist, (uint64_t)ph * total_atv + atv, 1);
+                    hist_add(P.hsum, atv, 1);
                 }
             }
         }
@@ -249,8 +285,12 @@ cudaError_t launch_hist_scan(const Params &P, uint32_t w, uint32_t *pool, uint32
     *launches += 1;
     return dispatch_w(w, [&](auto wb) {
         constexpr int WB = decltype(wb)::value;
-        auto kern = fuse ? (v8 ? hist_scan_kernel<WB, true, 8> : hist_scan_kernel<WB, true, 1>)
-                         : (v8 ? hist_scan_kernel<WB, false, 8> : hist_scan_kernel<WB, false, 1>);
+        // a window of all k slices reads the running sums
+        const bool sum = kp == P.k;
+        auto kern = fuse ? (sum ? (v8 ? hist_scan_kernel<WB, true, 8, true> : hist_scan_kernel<WB, true, 1, true>)
+                                : (v8 ? hist_scan_kernel<WB, true, 8, false> : hist_scan_kernel<WB, true, 1, false>))
+                         : (sum ? (v8 ? hist_scan_kernel<WB, false, 8, true> : hist_scan_kernel<WB, false, 1, true>)
+                                : (v8 ? hist_scan_kernel<WB, false, 8, false> : hist_scan_kernel<WB, false, 1, false>));
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
@@ -268,6 +308,8 @@ cudaError_t launch_hist_rebuild(const Params &P, uint32_t w, const uint32_t *poo
 {
     const uint32_t total = P.r << P.E_log2;
     cudaError_t e = cudaMemsetAsync(P.hist, 0, (size_t)P.k2 * total * sizeof(uint16_t), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(P.hsum, 0, (size_t)total * sizeof(uint16_t), s);
     if (e != cudaSuccess)
         return e;
     *launches += 1;

@@ -161,7 +161,8 @@ __device__ __forceinline__ bool claim_key(const Params &P, uint32_t gen, uint32_
 // compare-and-swap, which tells its old value f; if this lane changed it,
 // the count of the open slice's phase gains one and, if f was set less than
 // k slices ago, the count of f's slice loses one (a count older than that
-// is outside every window and is zeroed before its phase comes round again).
+// is outside every window and is zeroed before its phase comes round again);
+// otherwise the ATV's sum over the window gains one.
 __device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, uint32_t old, uint32_t sh, uint32_t val,
                                                uint32_t fm, uint32_t c0, uint32_t atv)
 {
@@ -178,14 +179,19 @@ __device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, 
     }
     const uint64_t n_atv = (uint64_t)P.r << P.E_log2;
     hist_add(P.hist, (uint64_t)c0 * n_atv + atv, 1);
+    bool in_window = false;
     if (f != P.k2) {
         uint32_t age = val + P.k2 - f;  // (ACT now - ACT then) mod 2k: slices since f was set
         age = age >= P.k2 ? age - P.k2 : age;
         if (age < P.k) {
             const uint32_t ph = c0 >= age ? c0 - age : c0 + P.k2 - age;
             hist_add(P.hist, (uint64_t)ph * n_atv + atv, -1);
+            in_window = true;
         }
     }
+    // the ATV's window sum gains the AT unless it moved within the window
+    if (!in_window)
+        hist_add(P.hsum, atv, 1);
 }
 
 // Algorithm 3 for one key (aip, h = BH(bip)) of this lane, if ok: f(aip), the

@@ -39,6 +39,11 @@ struct Params {
     // ASSE_COUNTER_AT_HIST: per ATV, the ATs last set in each slice phase
     // t mod 2k, phase-major ([2k][r * E] 16-bit counts); null otherwise.
     uint16_t *hist;
+    // ASSE_COUNTER_AT_HIST: per ATV ([r * E] 16-bit), the ATs set in the
+    // latest k slices, i.e. the sum of the k latest phase counts, kept by the
+    // ingest and the refresh so the close of a full window reads one count
+    // per ATV; null otherwise.
+    uint16_t *hsum;
     // CTAs of a thread-block cluster sharing the ingest's table of seen keys (1, 2, 4, 8)
     uint32_t cl;
     // 1: the 2k ACT blocks of an ATV are stored in pairs (block_slot below);

@@ -367,11 +367,18 @@ __global__ void __launch_bounds__(256) refresh_kernel(Params P, uint32_t *pool, 
     const uint64_t total = (uint64_t)total_atv * nw;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (P.hist) {
-        // the slice counts of the opening slice's phase start again from zero:
-        // every AT they counted (set 2k slices ago) has been cleared by now
+        // the window sums lose the phase that leaves the window (c0 - k + 1
+        // mod 2k), and the slice counts of the opening slice's phase start
+        // again from zero: every AT they counted (set 2k slices ago) has been
+        // cleared by now
+        const uint32_t c0 = ctl->c0;
+        const uint32_t leave = c0 + P.k + 1 >= P.k2 ? c0 + P.k + 1 - P.k2 : c0 + P.k + 1;
+        const uint16_t *hl = P.hist + (uint64_t)leave * total_atv;
         uint16_t *hz = P.hist + (uint64_t)R.c0n * total_atv;
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_atv; i += stride)
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_atv; i += stride) {
+            P.hsum[i] = (uint16_t)(P.hsum[i] - hl[i]);
             hz[i] = 0;
+        }
     }
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
         const uint64_t atv = idx / nw;
