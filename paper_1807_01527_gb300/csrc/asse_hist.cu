@@ -1,16 +1,18 @@
 // The close of a pool with slice counts (ASSE_COUNTER_AT_HIST).
 //
 // The ingest keeps, for every ATV, how many of its ATs each slice phase
-// (t mod 2k) set last (asse_ingest.cu).  An AT is active in the window of the
+// (t mod 2k) set last, and the sum of those counts over the window of the
+// latest k slices (asse_ingest.cu).  An AT is active in the window of the
 // latest k' slices iff it was set in one of them (Sec. 3), so |ATV|^{k'} is
-// the sum of the counts of the k' latest phases: one 2-byte read per ATV and
-// phase, coalesced across the ATVs (the counts are phase-major), instead of
-// the whole ATV.  The row-frame loads and the super-ATV lists follow as in
-// the full scan; only a super ATV's words are read, to build its g-bit active
-// mask for Algorithm 5.  In the close of a slice the same kernel then runs
-// the refresh of the two checked blocks (Algorithm 2) and zeroes the counts
-// of the opening slice's phase; the stepwise scan leaves both to the refresh
-// kernel of asse_advance.
+// the window sum for k' = k (one 2-byte read per ATV), or the sum of the
+// counts of the k' latest phases (2 bytes per ATV and phase, coalesced across
+// the ATVs: the counts are phase-major), instead of the whole ATV.  The
+// row-frame loads and the super-ATV lists follow as in the full scan; only a
+// super ATV's words are read, to build its g-bit active mask for Algorithm 5.
+// In the close of a slice the same kernel then runs the refresh of the two
+// checked blocks (Algorithm 2), takes the phase leaving the window out of the
+// sums and zeroes the counts of the opening slice's phase; the stepwise scan
+// leaves all three to the refresh kernel of asse_advance.
 #include <cuda_runtime.h>
 
 #include <cstdint>
