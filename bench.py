@@ -41,7 +41,7 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 # as null (the kernel has changed since the capture).
 TRAFFIC = {
     ("long", "hist", "ingest"): (1315014152, "d2db03fbd6a6"),
-    ("long", "hist", "hist_scan"): (147243248, "e75cda0555d3"),
+    ("long", "hist", "hist_scan"): (147243248, "b4b745c1cca5"),
     ("link", "at", "ingest"): (201394944, "d2db03fbd6a6"),
     ("link", "at", "scan"): (96553728, "4571ec86596b"),
     ("long", "at", "scan"): (1081540752, "4571ec86596b"),
