@@ -157,26 +157,14 @@ __device__ __forceinline__ bool claim_key(const Params &P, uint32_t gen, uint32_
     return exch_l2_hint(slot, want, pol) != want;
 }
 
-// SetAT with slice counts (ASSE_COUNTER_AT_HIST): the field is set with a
-// compare-and-swap, which tells its old value f; if this lane changed it,
-// the count of the open slice's phase gains one and, if f was set less than
-// k slices ago, the count of f's slice loses one (a count older than that
-// is outside every window and is zeroed before its phase comes round again);
-// otherwise the ATV's sum over the window gains one.
-__device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, uint32_t old, uint32_t sh, uint32_t val,
-                                               uint32_t fm, uint32_t c0, uint32_t atv)
+// Slice counts (ASSE_COUNTER_AT_HIST) after this lane changed a field of ATV
+// atv from f to the slice's value val: the count of the open slice's phase
+// gains one and, if f was set less than k slices ago, the count of f's slice
+// loses one (a count older than that is outside every window and is zeroed
+// before its phase comes round again); otherwise the ATV's sum over the
+// window gains one.
+__device__ __forceinline__ void hist_moved(const Params &P, uint32_t f, uint32_t val, uint32_t c0, uint32_t atv)
 {
-    uint32_t f;
-    for (;;) {
-        f = (old >> sh) & fm;
-        if (f == val)
-            return;  // already the slice's value: nothing changes
-        const uint32_t nw = (old & ~(fm << sh)) | (val << sh);
-        const uint32_t prev = atomicCAS(addr, old, nw);
-        if (prev == old)
-            break;
-        old = prev;
-    }
     const uint64_t n_atv = (uint64_t)P.r << P.E_log2;
     hist_add(P.hist, (uint64_t)c0 * n_atv + atv, 1);
     bool in_window = false;
@@ -192,6 +180,27 @@ __device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, 
     // the ATV's window sum gains the AT unless it moved within the window
     if (!in_window)
         hist_add(P.hsum, atv, 1);
+}
+
+// SetAT with slice counts: the field is set with a compare-and-swap, which
+// tells its old value; old is the word as last seen (a read, or a failed
+// compare-and-swap), retried until this lane changes the field or finds it
+// already holding val.
+__device__ __forceinline__ void set_field_hist(const Params &P, uint32_t *addr, uint32_t old, uint32_t sh, uint32_t val,
+                                               uint32_t fm, uint32_t c0, uint32_t atv)
+{
+    uint32_t f;
+    for (;;) {
+        f = (old >> sh) & fm;
+        if (f == val)
+            return;  // already the slice's value: nothing changes
+        const uint32_t nw = (old & ~(fm << sh)) | (val << sh);
+        const uint32_t prev = atomicCAS(addr, old, nw);
+        if (prev == old)
+            break;
+        old = prev;
+    }
+    hist_moved(P, f, val, c0, atv);
 }
 
 // Algorithm 3 for one key (aip, h = BH(bip)) of this lane, if ok: f(aip), the
@@ -223,14 +232,32 @@ __device__ __forceinline__ void set_key(const Params &P, uint32_t *pool, uint32_
     for (int i = 0; i < RM; i++)
         if (i < r)
             o[i] = *a[i];
+    if constexpr (HIST) {
+        // the r compare-and-swaps issued together; one that lost a race with
+        // another lane's change of the same word retries on what it returned
+        uint32_t prev[RM];
 #pragma unroll
-    for (int i = 0; i < RM; i++) {
-        if (i < r) {
-            if constexpr (HIST)
-                set_field_hist(P, a[i], o[i], sh, val, FM, c0, (uint32_t)((a[i] - pool) / P.Wd));
-            else
-                set_field(a[i], o[i], sh, val, FM);
+        for (int i = 0; i < RM; i++)
+            if (i < r)
+                prev[i] = ((o[i] >> sh) & FM) != val ? atomicCAS(a[i], o[i], (o[i] & ~(FM << sh)) | (val << sh)) : o[i];
+#pragma unroll
+        for (int i = 0; i < RM; i++) {
+            if (i < r) {
+                const uint32_t f = (o[i] >> sh) & FM;
+                if (f == val)
+                    continue;
+                const uint32_t atv = (uint32_t)((a[i] - pool) / P.Wd);
+                if (prev[i] == o[i])
+                    hist_moved(P, f, val, c0, atv);
+                else
+                    set_field_hist(P, a[i], prev[i], sh, val, FM, c0, atv);
+            }
         }
+    } else {
+#pragma unroll
+        for (int i = 0; i < RM; i++)
+            if (i < r)
+                set_field(a[i], o[i], sh, val, FM);
     }
 }
 
