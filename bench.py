@@ -374,7 +374,8 @@ def run_learned(args):
     build.build()
     w = synth.workload(args.workload, seed=1)
     stream = torch.cuda.current_stream()
-    pool = asse.Pool(w.params, stream=stream.cuda_stream)
+    counter = counter_for(args, w)
+    pool = asse.Pool(w.params, counter=counter, stream=stream.cuda_stream)
     pairs = w.pairs(0) if w.n_per_slice <= (8 << 20) else gen_batch_gpu(w.n_per_slice, 3, w.n_hosts, w.zipf)
     src = torch.from_numpy(pairs.view(np.int32)).cuda() if isinstance(pairs, np.ndarray) else pairs
     pool.ingest(src)
@@ -410,7 +411,9 @@ def run_learned(args):
     line = {"metric": "learned per-ATV inference: feature rows + MLP per scanned slice", "value": rows / (t_feat + t_mlp),
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "mode": "learned",
             "ms_per_step": 1e3 * (t_feat + t_mlp), "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-            "config": dict(workload_desc(w), rows_per_step=rows,
+            "config": dict(workload_desc(w), rows_per_step=rows, counter=counter.upper(),
+                           features=("from the slice counts (k' per ATV)" if counter == "hist" else
+                                     "from the pool words"),
                            l2="feature rows %d MB (%s the 129 MB L2), re-read each step"
                               % (rows * 160 >> 20, "within" if rows * 160 < (100 << 20) else "larger than")),
             "kernel_ms": {"features": 1e3 * t_feat, "mlp_tcgen05": 1e3 * t_mlp},

@@ -36,8 +36,12 @@ def _bf16(x):
     return omlp.bf16(x)
 
 
-@pytest.mark.parametrize("k,g,counter", [(6, 150, "at"), (10, 512, "at"), (5, 77, "ace")])
+@pytest.mark.parametrize("k,g,counter", [(6, 150, "at"), (10, 512, "at"), (5, 77, "ace"), (6, 150, "hist"),
+                                         (20, 256, "hist")])
 def test_features_match_definition(mods, k, g, counter):
+    """Feature rows of a pool against oracle/features.py on the oracle's state
+    (slice-count pools build them from their counts, the others from their
+    words), every slice of two windows' worth, full and shorter windows."""
     asse, oracle, omlp, torch = mods
     from oracle import features as ofeat
     p = dict(k=k, theta=max(4, g // 3), g=g, r=4, c=9, u=2, s=7, **synth.method_keys(3))
