@@ -551,12 +551,12 @@ def run_accuracy(args):
     """Detection accuracy on the workload's ground truth (exact window
     cardinalities, Sec. 2.1), as FPR / FNR / FTR (Sec. 5), of:
       - the sliding pool with Eq. 4 (the paper's method), every slice;
-      - the same candidates judged by the learned candidate model instead of
+      - the same candidates decided by the learned candidate model instead of
         Eq. 4 (trained here on synthetic candidate states shaped like the
         pool: k, g, r and the row loads the first window shows);
       - the discrete-window mode (1-bit aging counters, k = 1, reset after
         every window of k slices) at equal memory: the same words per ATV,
-        so 32 x words ATs of one bit each, judged at the end of each window."""
+        so 32 x words ATs of one bit each, read at the end of each window."""
     import concurrent.futures as cf
     import multiprocessing as mp
     w = synth.workload(args.workload, seed=1)

@@ -5,7 +5,7 @@
  * the ATV fills.  This model maps the state of one ATV to its log-cardinality
  * with a small MLP (features -> 256 -> 256 -> 1, ReLU), trained and run on the
  * GPU by the library's own BF16-in / FP32-accumulate kernels; Eq. 2 remains
- * the fallback outside the training range and the baseline it is judged by.
+ * the fallback outside the training range and the baseline it is compared with.
  *
  * Conventions as in asse.h (status codes, where = ASSE_HOST / ASSE_DEVICE,
  * stream-ordered asynchronous work unless stated).
