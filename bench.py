@@ -42,8 +42,8 @@ MLP_FLOP_PER_ROW = 2 * (68 * 256 + 256 * 256 + 256)
 TRAFFIC = {
     ("long", "hist", "ingest"): (1295601920, "d0191276ba84"),
     ("long", "hist", "hist_scan"): (147243248, "bd35d6abdfed"),
-    ("link", "at", "ingest"): (201394944, "5262e2878bd3"),
-    ("link", "at", "scan"): (96553728, "7fe98d3eebca"),
+    ("link", "at", "ingest"): (201379072, "d0191276ba84"),
+    ("link", "at", "scan"): (96883456, "7fe98d3eebca"),
     ("long", "at", "scan"): (1081540752, "7fe98d3eebca"),
 }
 KERNEL_SOURCES = {

@@ -143,12 +143,15 @@ def test_mix_equals_alone_with_admission(mods):
     srv.destroy()
 
 
-def test_learned_inference_in_close_graphs(mods):
+@pytest.mark.parametrize("counter", ["at", "hist"])
+def test_learned_inference_in_close_graphs(mods, counter):
     """A model attached to a stream runs inside its captured close graphs
     (feature rows, tensor-core MLP, Eq. 2 fallback between the scan and the
     refresh): every close's learned estimates equal asse_estimate_learned on
     a plain pool fed the same batches, and the reports still equal the
-    oracle's (the refresh now runs as its own kernel after the restore)."""
+    oracle's (the refresh now runs as its own kernel after the restore).
+    With slice counts the feature rows come from the counts, C0 read from
+    the device slice state as each graph replays."""
     asse, torch = mods
     k, g, elog = 10, 512, 12
     c, u, s = synth.column_split(elog, 4)
@@ -160,7 +163,7 @@ def test_learned_inference_in_close_graphs(mods):
     model = asse.MLP(seed=3, stream=stream)
     rows = 4 << elog
     # the plain pool path: scan, learned estimate, restore, refresh
-    pool = asse.Pool(p, stream=stream)
+    pool = asse.Pool(p, stream=stream, counter=counter)
     # the model's outputs moved to straddle max_log_n, so that the model and
     # the fallback both serve some ATVs
     for b in slices[0]:
@@ -172,7 +175,7 @@ def test_learned_inference_in_close_graphs(mods):
     model.set_params(prm)
     max_log_n = 2.0
     pool.close()
-    pool = asse.Pool(p, stream=stream)
+    pool = asse.Pool(p, stream=stream, counter=counter)
     want_est, want_nfb = [], []
     for batches in slices:
         for b in batches:
@@ -185,7 +188,7 @@ def test_learned_inference_in_close_graphs(mods):
         pool.advance()
     pool.close()
     srv = asse.Server(1 << 40)
-    sid = srv.open(p, k, max_batch=40000)
+    sid = srv.open(p, k, max_batch=40000, counter=counter)
     srv.attach_model(sid, model, max_log_n)
     for t, (batches, rows_want) in enumerate(zip(slices, _oracle_reports(p, k, slices))):
         for j, b in enumerate(batches):
