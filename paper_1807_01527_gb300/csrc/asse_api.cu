@@ -55,6 +55,11 @@ struct asse_pool {
     uint64_t report_host_cap = 0;
     int report_host_valid = 0;
     cudaEvent_t close_done = nullptr;  // recorded after those copies: a report waits for its close only
+    // the copies of a close's status and report to pinned memory run on their
+    // own stream, after `closed`, so the next batch's ingest does not wait
+    // for them; the next close waits for close_done before it rewrites them
+    cudaStream_t d2h_stream = nullptr;
+    cudaEvent_t closed = nullptr;
     // asse_set_timing: events around the scan and the restore of each close
     cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
     int timing = 0, timed = 0;
@@ -205,6 +210,15 @@ __global__ void init_pool_kernel(uint32_t *pool, uint64_t nwords, uint32_t Wd, u
     }
 }
 
+// Work of the pool's stream that rewrites the status or the report waits
+// until the last close's copies of them (on d2h_stream) have read them.  Not
+// for captured graphs (their closes copy on their own stream in order).
+int wait_close_copies(asse_pool *p)
+{
+    CK(p, cudaStreamWaitEvent(p->stream, p->close_done, 0));
+    return ASSE_OK;
+}
+
 int reset_close_state(asse_pool *p)
 {
     CK(p, launch_reset(p->aat, p->sa_n, p->cfg.r * p->P.nf, p->status, p->stream, &p->launches));
@@ -226,6 +240,7 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
         return fail(p, ASSE_ESTATE, "no restore since the last scan");
     const bool early = reported && where != ASSE_DEVICE && p->report_host_valid && p->sel == 0;
     if (!early) {
+        CK(p, cudaEventSynchronize(p->close_done));  // no close's copy is still writing status_host
         CK(p, cudaMemcpyAsync(p->status_host, scan_out_w(p, p->sel).status, sizeof(Status), cudaMemcpyDeviceToHost,
                               p->stream));
         CK(p, cudaStreamSynchronize(p->stream));
@@ -294,6 +309,10 @@ void free_all(asse_pool *p)
         cudaFreeHost(p->report_host);
     if (p->close_done)
         cudaEventDestroy(p->close_done);
+    if (p->closed)
+        cudaEventDestroy(p->closed);
+    if (p->d2h_stream)
+        cudaStreamDestroy(p->d2h_stream);
     for (cudaEvent_t ev : p->tev)
         if (ev)
             cudaEventDestroy(ev);
@@ -582,6 +601,10 @@ int asse_create(const asse_config *cfg, void *stream, asse_pool **out)
         e = cudaEventCreateWithFlags(&p->close_done, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&p->closed, cudaEventDisableTiming);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
         e = cudaEventCreateWithFlags(&p->copied[i], cudaEventDisableTiming);
         if (e == cudaSuccess)
@@ -637,6 +660,7 @@ void asse_destroy(asse_pool *pool)
         return;
     cudaStreamSynchronize(pool->stream);
     cudaStreamSynchronize(pool->copy_stream);
+    cudaStreamSynchronize(pool->d2h_stream);
     free_all(pool);
     delete pool;
 }
@@ -698,6 +722,8 @@ int asse_scan(asse_pool *p, uint32_t kp)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (int rc = check_kp(p, kp))
         return rc;
+    if (int rc = wait_close_copies(p))
+        return rc;
     if (int rc = pool_enqueue_scan(p, kp))
         return rc;
     p->n_windows = 1;
@@ -719,6 +745,8 @@ int asse_restore(asse_pool *p)
     if (!p->scanned)
         return fail(p, ASSE_ESTATE, "restore needs a scan of the open slice");
     p->report_host_valid = 0;
+    if (int rc = wait_close_copies(p))
+        return rc;
     CK(p, launch_restore(p->P, scan_out(p), p->scratch, p->cap, p->csip, p->report, p->out_cap, p->stream,
                          &p->launches));
     p->restored = 1;
@@ -742,14 +770,18 @@ int asse_close_slice(asse_pool *p, uint32_t kp)
         return fail(nullptr, ASSE_EINVAL, "pool is NULL");
     if (int rc = check_kp(p, kp))
         return rc;
+    if (int rc = wait_close_copies(p))
+        return rc;
     if (int rc = pool_enqueue_close(p, kp, p->timing != 0))
         return rc;
     pool_after_close(p, kp);
     p->timed = p->timing;
-    CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->stream));
+    CK(p, cudaEventRecord(p->closed, p->stream));
+    CK(p, cudaStreamWaitEvent(p->d2h_stream, p->closed, 0));
+    CK(p, cudaMemcpyAsync(p->status_host, p->status, sizeof(Status), cudaMemcpyDeviceToHost, p->d2h_stream));
     CK(p, cudaMemcpyAsync(p->report_host, p->report, p->report_host_cap * sizeof(asse_superpoint),
-                          cudaMemcpyDeviceToHost, p->stream));
-    CK(p, cudaEventRecord(p->close_done, p->stream));
+                          cudaMemcpyDeviceToHost, p->d2h_stream));
+    CK(p, cudaEventRecord(p->close_done, p->d2h_stream));
     p->report_host_valid = 1;
     return ASSE_OK;
 }
@@ -793,6 +825,8 @@ int asse_close_slice_multi(asse_pool *p, const uint32_t *kps, uint32_t n_windows
                                                   : cuda_fail(p, e, "window outputs");
         }
     }
+    if (int rc = wait_close_copies(p))
+        return rc;
     ScanWindows W{};
     W.n = n_windows;
     for (uint32_t m = 0; m < n_windows; m++) {
