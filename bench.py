@@ -165,6 +165,15 @@ def oracle_slice_time(w, pairs, counter: str = "at", orc=None):
     return dt, cores, text, orc
 
 
+def line_config(w, args, world: int) -> dict:
+    """The `config` of the main JSON line, the same for the device leg and
+    the reference (oracle) leg of one command line."""
+    return dict(workload_desc(w), counter=counter_for(args, w).upper(), key_table=args.key_table,
+                cluster=args.cluster, parallelism="replicas" if world > 1 else "single",
+                l2="inputs cycle over distinct slices held in memory, together larger than the L2 cache "
+                   "(inputs_cycled); the pool state stays resident across steps")
+
+
 def run_reference(args, w):
     """--impl reference: the oracle on every host core, each step one whole
     slice of the workload (the slices cycled as in the GPU leg)."""
@@ -186,7 +195,8 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pkts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_desc(w),
+            "config": line_config(w, args, int(os.environ.get("WORLD_SIZE", "1"))),
+            "inputs_cycled": {"slices": n_cycled, "MB": sum(p.nbytes for p in host[:n_cycled]) >> 20},
             "cpu_baseline": {"value": value, "unit": "pkts/s", "cores": cores, "kind": "oracle", "sample": text},
             "e2e": {"value": value, "unit": "pkts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -972,12 +982,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(workload_desc(w), counter=counter_for(args, w).upper(), key_table=args.key_table,
-                           cluster=args.cluster,
-                           parallelism="replicas" if world > 1 else "single",
-                           l2="inputs cycle over %d distinct slices (%d MB) held in HBM, more than L2; the pool "
-                              "state stays resident across steps" % (m["n_cycled"],
-                                                                     sum(p.nbytes for p in m["host"]) >> 20)),
+            "config": line_config(w, args, world),
+            "inputs_cycled": {"slices": m["n_cycled"], "MB": sum(p.nbytes for p in m["host"]) >> 20},
             "roofline": dict(rl[dominant], dominant=True),
             "roofline_other": {k: v for k, v in rl.items() if k != dominant},
             "e2e": {"value": e2e_pairs / e2e_elapsed, "unit": "pkts/s",

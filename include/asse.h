@@ -50,6 +50,13 @@ extern "C" {
 #define ASSE_ECAPACITY 3 /* an output or the restore scratch is too small */
 #define ASSE_ECUDA 4     /* a CUDA runtime call or kernel launch failed */
 #define ASSE_ESTATE 5    /* call out of order (e.g. restore before scan) */
+/* 6 is ASSE_EAGAIN of asse_serve.h. */
+#define ASSE_ETIMEOUT 7  /* a bounded device-side wait gave up: a bulk copy or a
+                          * tensor-core pipeline stage did not complete within
+                          * about 2 s of SM clock.  The kernel returned instead
+                          * of hanging and the CUDA context stays usable, but the
+                          * outputs of that work are invalid (reload the pool
+                          * from a snapshot or recreate it). */
 
 /* Buffer locations. */
 #define ASSE_HOST 0
@@ -296,7 +303,8 @@ ASSE_API int asse_estimate(asse_pool *pool, const uint32_t *aips, uint64_t n, as
  * synchronises the stream.  Returns ECAPACITY if cap < count, or
  * if the restore overflowed restore_cap (then *n_out is the number of
  * column tuples the overflowing join level needed, a lower bound on the
- * capacity to configure, and out is not written).  Errors: ESTATE, ECUDA. */
+ * capacity to configure, and out is not written).  Errors: ESTATE,
+ * ETIMEOUT (a bounded wait of the scan gave up; the lists are invalid), ECUDA. */
 ASSE_API int asse_report(asse_pool *pool, asse_superpoint *out, uint64_t cap, uint64_t *n_out, int where);
 
 /* As asse_report, but every restored candidate (CSIP, Algorithm 4), reported
@@ -338,6 +346,20 @@ ASSE_API int asse_load(asse_pool *pool, const void *src, uint64_t n);
  * traffic is r random words per pair new to the slice.  Does not
  * synchronise.  Errors: EINVAL, ECUDA. */
 ASSE_API int asse_probe_random_reads(asse_pool *pool, uint64_t n_reads, uint64_t *n_issued);
+
+/* Self-test of the device-side waits, no counterpart in the paper: the
+ * kernels that stage data with bulk copies or drive the tensor cores wait on
+ * mbarriers with a bound, and report ASSE_ETIMEOUT instead of hanging when a
+ * wait gives up.  This call runs that wait once in a one-thread kernel on
+ * `stream` (a cudaStream_t as void*, NULL = legacy default stream), on an
+ * mbarrier that the kernel completes first if `complete` != 0 and that
+ * nothing completes otherwise, with a bound of limit_cycles SM clock cycles
+ * (1 .. 2^36).  *cycles_waited (may be NULL) receives the cycles the wait
+ * took.  The result travels through one fixed device variable, so calls
+ * that overlap on a device race on it.  Synchronises the stream.
+ * Returns ASSE_OK if the wait completed, ASSE_ETIMEOUT if it gave up.
+ * Errors: EINVAL (limit out of range), ECUDA. */
+ASSE_API int asse_probe_bounded_wait(void *stream, uint64_t limit_cycles, int complete, uint64_t *cycles_waited);
 
 /* Measurement aid, no counterpart in the paper: with on != 0, every later
  * asse_close_slice records CUDA events on the pool's stream before and after

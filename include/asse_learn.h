@@ -126,8 +126,9 @@ ASSE_API int asse_mlp_set_params(asse_mlp *mlp, const float *host);
  * Errors: EINVAL (misaligned x_dev), ECUDA. */
 ASSE_API int asse_mlp_forward(asse_mlp *mlp, const uint16_t *x_dev, uint64_t n, float *y_dev);
 
-/* Synchronise the model's stream; ASSE_ECUDA if a kernel of this model gave
- * up a bounded wait (its outputs are then invalid). */
+/* Synchronise the model's stream; ASSE_ETIMEOUT if a kernel of this model
+ * gave up a bounded wait (its outputs are then invalid), ASSE_ECUDA if a CUDA
+ * call failed. */
 ASSE_API int asse_mlp_check(asse_mlp *mlp);
 
 /* Training losses over n rows with targets t_i = ln(cardinality):

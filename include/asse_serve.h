@@ -66,7 +66,8 @@ ASSE_API int asse_server_submit(asse_server *srv, uint32_t id, const uint32_t *p
  * return ASSE_OK; ASSE_EAGAIN if it has not finished or none is pending.
  * Returns ASSE_ECAPACITY (with *n_out) if the report did not fit cap, the
  * per-close copy limit (restore_cap entries), or the restore's capacity.
- * Errors: EINVAL, EAGAIN, ECAPACITY, ECUDA. */
+ * Errors: EINVAL, EAGAIN, ECAPACITY, ETIMEOUT (a bounded wait of that close's
+ * scan gave up; its report is invalid), ECUDA. */
 ASSE_API int asse_server_poll(asse_server *srv, uint32_t id, asse_superpoint *out, uint64_t cap, uint64_t *n_out,
                               uint64_t *slice, float *latency_ms);
 

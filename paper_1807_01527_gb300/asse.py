@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libasse.so")
 
-OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE, EAGAIN = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ECAPACITY, ECUDA, ESTATE, EAGAIN, ETIMEOUT = 0, 1, 2, 3, 4, 5, 6, 7
 HOST, DEVICE = 0, 1
 COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED, COUNTER_AT_HIST = 0, 1, 2, 3
 COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED, "hist": COUNTER_AT_HIST}
@@ -72,6 +72,7 @@ EXPORTS = {
     "asse_snapshot": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
     "asse_load": (i32, [vp, vp, u64]),
     "asse_probe_random_reads": (i32, [vp, u64, ctypes.POINTER(u64)]),
+    "asse_probe_bounded_wait": (i32, [vp, u64, i32, ctypes.POINTER(u64)]),
     "asse_set_timing": (i32, [vp, i32]),
     "asse_close_timing": (i32, [vp, vp]),
     "asse_launches": (u64, [vp]),
@@ -441,6 +442,18 @@ class Pool:
         x = torch.empty((self.r * self._info["E"], FEAT), dtype=torch.bfloat16, device="cuda")
         self._check(lib().asse_features(self._h, vp(x.data_ptr())))
         return x
+
+
+def probe_bounded_wait(limit_cycles: int, complete: bool) -> tuple[int, int]:
+    """Run the library's bounded mbarrier wait once on the current torch
+    stream (asse_probe_bounded_wait); returns (status, cycles waited), status
+    OK if the barrier completed and ETIMEOUT if the wait gave up."""
+    waited = u64(0)
+    rc = lib().asse_probe_bounded_wait(vp(_current_stream()), int(limit_cycles), int(bool(complete)),
+                                       ctypes.byref(waited))
+    if rc not in (OK, ETIMEOUT):
+        raise AsseError(rc, "bounded-wait probe failed")
+    return rc, int(waited.value)
 
 
 def synth_candidates(cfg: dict, first: int, n: int, stream: int | None = None):

@@ -251,7 +251,7 @@ int read_list(asse_pool *p, bool reported, asse_superpoint *out, uint64_t cap, u
     }
     const Status st = *p->status_host;
     if (st.error)
-        return fail(p, ASSE_ECUDA, "a bounded device wait of the scan gave up (bulk copy did not complete)");
+        return fail(p, ASSE_ETIMEOUT, "a bounded device wait of the scan gave up (bulk copy did not complete)");
     if (st.overflow) {
         *n_out = st.needed;
         char buf[200];
@@ -488,6 +488,8 @@ const char *asse_strerror(int status)
     case ASSE_ECAPACITY: return "ASSE_ECAPACITY";
     case ASSE_ECUDA: return "ASSE_ECUDA";
     case ASSE_ESTATE: return "ASSE_ESTATE";
+    case 6: return "ASSE_EAGAIN";
+    case ASSE_ETIMEOUT: return "ASSE_ETIMEOUT";
     default: return "unknown status";
     }
 }

@@ -654,7 +654,7 @@ int asse_mlp_check(asse_mlp *m)
     int flag = 0;
     MCK(m, cudaMemcpy(&flag, m->error, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag)
-        return mlp_fail(m, ASSE_ECUDA, "a tensor-core MLP kernel gave up waiting for its pipeline");
+        return mlp_fail(m, ASSE_ETIMEOUT, "a tensor-core MLP kernel gave up waiting for its pipeline");
     return ASSE_OK;
 }
 

@@ -4,11 +4,17 @@
 // random words per pair new to the slice), so this rate, timed by the caller
 // around asse_probe_random_reads, is the random-access roofline the ingest is
 // compared with beside the streaming HBM bandwidth.
+//
+// Also a self-test of the bounded device waits (asse_probe_bounded_wait): the
+// mbarrier try-wait loop with a clock bound, run on a barrier that may never
+// complete, so the give-up path and its ASSE_ETIMEOUT status can be exercised
+// without hanging the GPU.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "asse_internal.h"
+#include "asse_ptx.cuh"
 
 namespace asse {
 
@@ -46,6 +52,35 @@ __global__ void __launch_bounds__(PROBE_THREADS) random_read_kernel(const uint32
         atomicXor(&g_probe_sink, (unsigned long long)acc);
 }
 
+// Result of the bounded-wait self-test: [0] 1 if the wait completed, 2 if it
+// gave up; [1] the cycles it took.
+__device__ unsigned long long g_wait_result[2];
+
+// One thread: an mbarrier expecting one arrival, which this thread makes
+// first only when `complete` is set; then the same try-wait loop with a
+// clock bound that the staging and tensor-core kernels use, here with the
+// caller's bound.
+__global__ void bounded_wait_kernel(long long limit, int complete)
+{
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (complete)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    const long long t0 = clock64();
+    bool done = false;
+    for (;;) {
+        if (mbar_try_wait(&bar, 0)) {
+            done = true;
+            break;
+        }
+        if (clock64() - t0 > limit)
+            break;
+    }
+    g_wait_result[0] = done ? 1ull : 2ull;
+    g_wait_result[1] = (unsigned long long)(clock64() - t0);
+}
+
 }  // namespace
 
 cudaError_t launch_random_reads(const uint32_t *buf, uint64_t n_words, uint64_t n_reads, int sms, cudaStream_t s,
@@ -64,3 +99,23 @@ cudaError_t launch_random_reads(const uint32_t *buf, uint64_t n_words, uint64_t 
 }
 
 }  // namespace asse
+
+extern "C" int asse_probe_bounded_wait(void *stream, uint64_t limit_cycles, int complete, uint64_t *cycles_waited)
+{
+    using namespace asse;
+    if (limit_cycles < 1 || limit_cycles > (1ull << 36))
+        return ASSE_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long res[2] = {0, 0};
+    if (cudaMemcpyToSymbolAsync(g_wait_result, res, sizeof res, 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return ASSE_ECUDA;
+    bounded_wait_kernel<<<1, 1, 0, s>>>((long long)limit_cycles, complete);
+    if (cudaGetLastError() != cudaSuccess)
+        return ASSE_ECUDA;
+    if (cudaMemcpyFromSymbolAsync(res, g_wait_result, sizeof res, 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || res[0] == 0)
+        return ASSE_ECUDA;
+    if (cycles_waited)
+        *cycles_waited = res[1];
+    return res[0] == 2 ? ASSE_ETIMEOUT : ASSE_OK;
+}

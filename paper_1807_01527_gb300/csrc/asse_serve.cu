@@ -344,7 +344,7 @@ int asse_server_poll(asse_server *srv, uint32_t id, asse_superpoint *out, uint64
     st->head = (st->head + 1) % ASSE_SERVE_RING;
     st->count--;
     if (stt.error)
-        return sfail(srv, ASSE_ECUDA, "a bounded device wait of the scan gave up");
+        return sfail(srv, ASSE_ETIMEOUT, "a bounded device wait of the scan gave up");
     if (stt.overflow) {
         *n_out = stt.needed;
         return sfail(srv, ASSE_ECAPACITY, "restore capacity exceeded");
