@@ -610,11 +610,9 @@ def run_accuracy(args):
         if t >= k - 1:
             true_sp = truth.super_points(keys[t - k + 1:t + 1], w.theta)
             res["eq4"].append(truth.error_rates({int(a) for a in cand["aip"][cand["est"] >= w.theta]}, true_sp))
-            learned = set()
-            if cand.size:
-                y = model.forward(sliding.candidate_features(cand["aip"])).cpu().numpy().astype(np.float64)
-                est = np.where(y <= max_log_n, np.exp(np.maximum(y, 0.0)), cand["est"].astype(np.float64))
-                learned = {int(a) for a in cand["aip"][est >= w.theta]}
+            # the same candidates decided on the device by the learned model
+            # (Eq. 4 where the model's output leaves its training range)
+            learned = {int(a) for a in sliding.report_learned(model, max_log_n)["aip"]}
             res["learned"].append(truth.error_rates(learned, true_sp))
         sliding.advance()
         if (t + 1) % k == 0:

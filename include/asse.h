@@ -89,6 +89,7 @@ extern "C" {
 /* Flags of asse_superpoint. */
 #define ASSE_SP_SATURATED 1u /* NAT == g: Eq. 4 is +infinity */
 #define ASSE_SP_REPORTED 2u  /* estimate >= theta */
+#define ASSE_SP_LEARNED 4u   /* est is the learned candidate estimate (asse_report_learned), not Eq. 4 */
 
 /* Pool parameters (Sec. 3 and Sec. 4.1).
  *  k       window size in slices (1..127); AT values are 0..2k, 2k inactive.

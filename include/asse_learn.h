@@ -97,6 +97,29 @@ ASSE_API int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64
  * Errors: ESTATE, EINVAL, ECUDA. */
 ASSE_API int asse_candidate_features(asse_pool *pool, const uint32_t *aips_dev, uint64_t n, uint16_t *x_dev);
 
+/* The report of the last restore with the learned candidate estimate in
+ * place of Eq. 4 (Sec. 4.3, Algorithm 5 and Eq. 4 decide the report of
+ * asse_report; this build's model replaces that last step).  For every
+ * candidate of CSIP (Algorithm 4): its feature row (as
+ * asse_candidate_features), the model mlp on it (tensor-core inference),
+ * and, where the model's output y is within its training range
+ * (y <= max_log_n), est = exp(max(y, 0)) with flags ASSE_SP_LEARNED, and
+ * ASSE_SP_REPORTED if est >= theta in FP32; elsewhere the candidate keeps its
+ * Eq. 4 estimate, flags and decision.  The reported candidates are written
+ * to out (host or device, `where`) in unspecified order, min(count, cap) of
+ * them, and *n_out receives the count.  Every step runs on the device; the
+ * call synchronises the pool's stream (it reads the candidate count first).
+ * Valid between asse_scan + asse_restore and asse_advance, as
+ * asse_features (after asse_close_slice the refresh has changed the
+ * state: ESTATE).  The model must use the pool's stream.  The library keeps
+ * the device workspace (about 200 bytes per candidate of the pool's list
+ * capacity) with the model, allocated on first use.
+ * Errors: EINVAL (NULL, negative max_log_n, other stream, k' > 64),
+ * ESTATE, ECAPACITY (cap < count, *n_out set; or the restore overflowed, as
+ * asse_report), ENOMEM, ETIMEOUT, ECUDA. */
+ASSE_API int asse_report_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, asse_superpoint *out,
+                                 uint64_t cap, uint64_t *n_out, int where);
+
 /* Synthetic candidate states first .. first+n-1: one host of cardinality n
  * (log-uniform in [1, 2^n_max_log2], spread over the k slices with random
  * shares) in r ATVs, each row with its own background (every AT set in each

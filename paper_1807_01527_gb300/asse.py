@@ -20,7 +20,7 @@ HOST, DEVICE = 0, 1
 COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED, COUNTER_AT_HIST = 0, 1, 2, 3
 COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED, "hist": COUNTER_AT_HIST}
 KEY_TABLE = {"auto": 0, "on": 1, "off": 2}
-SP_SATURATED, SP_REPORTED = 1, 2
+SP_SATURATED, SP_REPORTED, SP_LEARNED = 1, 2, 4
 
 u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
 
@@ -83,6 +83,7 @@ EXPORTS = {
     "asse_estimate_learned": (i32, [vp, vp, ctypes.c_float, vp, vp, vp]),
     "asse_synth_states": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
     "asse_candidate_features": (i32, [vp, vp, u64, vp]),
+    "asse_report_learned": (i32, [vp, vp, ctypes.c_float, vp, u64, ctypes.POINTER(u64), i32]),
     "asse_synth_candidates": (i32, [ctypes.POINTER(SynthCfg), u64, u64, vp, vp, vp, vp]),
     "asse_mlp_create": (i32, [u64, vp, ctypes.POINTER(vp)]),
     "asse_mlp_destroy": (None, [vp]),
@@ -434,6 +435,15 @@ class Pool:
         x = torch.empty((a.numel(), FEAT), dtype=torch.bfloat16, device="cuda")
         self._check(lib().asse_candidate_features(self._h, vp(a.data_ptr()), a.numel(), vp(x.data_ptr())))
         return x
+
+    def report_learned(self, mlp: "MLP", max_log_n: float, out=None):
+        """The report with the learned candidate estimate in place of Eq. 4
+        (asse_report_learned), between scan() + restore() and advance():
+        a structured array, or the count when out (a device tensor of
+        SuperPoint records) is given."""
+        fn = lambda h, o, cap, n, where: lib().asse_report_learned(h, mlp._h, ctypes.c_float(max_log_n), o, cap, n,
+                                                                   where)
+        return self._list(fn, out)
 
     def features(self):
         """Feature rows [r*E][FEAT] (torch bfloat16 on the device) of every

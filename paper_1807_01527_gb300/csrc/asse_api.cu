@@ -11,6 +11,7 @@
 #include <string>
 
 #include "asse_internal.h"
+#include "asse_pool_access.h"
 
 using namespace asse;
 
@@ -456,6 +457,8 @@ uint64_t pool_device_bytes(const asse_config *cfg)
            2 * cap * nf * sizeof(asse_superpoint) + sizeof(Status) + sizeof(SliceCtl) + 2 * stage * 8 +
            (klg ? sizeof(unsigned long long) << klg : 0);
 }
+
+uint64_t pool_list_cap(const asse_pool *p) { return p ? p->out_cap : 0; }
 
 int pool_feature_view(asse_pool *p, FeatureView *v)
 {

@@ -25,6 +25,7 @@
 #include "asse_device.cuh"
 #include "asse_features.cuh"
 #include "asse_mlp_tc.h"
+#include "asse_pool_access.h"
 #include "asse_synth.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -68,6 +69,48 @@ __global__ void learned_combine_kernel(const float *y, const uint16_t *cnt, uint
     fb = __reduce_add_sync(FULL_MASK, fb);
     if ((threadIdx.x & 31) == 0 && fb)
         atomicAdd(n_fallback, fb);
+}
+
+// ---------------------------------------------------------------- learned report
+
+// The host addresses of n candidate records, contiguous for the feature kernel.
+__global__ void cand_aips_kernel(const asse_superpoint *c, uint64_t n, uint32_t *aips)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        aips[i] = c[i].aip;
+}
+
+// The decision of asse_report_learned for each candidate: inside the model's
+// training range its estimate exp(max(y, 0)) and est >= theta, else the
+// candidate's Eq. 4 estimate and decision as restored.  The reported records
+// are packed into rep, each warp taking its places with one atomic.
+__global__ void learned_report_kernel(const asse_superpoint *cand, const float *y, uint64_t n, float max_log_n,
+                                      float theta, asse_superpoint *rep, unsigned long long *n_rep)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // one bound per warp, so that every lane takes part in the ballot
+    for (uint64_t base = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint64_t i = base + lane;
+        asse_superpoint sp{};
+        bool keep = false;
+        if (i < n) {
+            sp = cand[i];
+            const float yi = y[i];
+            if (yi <= max_log_n) {  // false for a NaN output: Eq. 4 stands
+                sp.est = expf(fmaxf(yi, 0.0f));
+                sp.flags = ASSE_SP_LEARNED | (sp.est >= theta ? ASSE_SP_REPORTED : 0u);
+            }
+            keep = (sp.flags & ASSE_SP_REPORTED) != 0;
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, keep);
+        unsigned long long at = 0;
+        if (lane == 0 && m)
+            at = atomicAdd(n_rep, (unsigned long long)__popc(m));
+        at = __shfl_sync(FULL_MASK, at, 0);
+        if (keep)
+            rep[at + __popc(m & ((1u << lane) - 1u))] = sp;
+    }
 }
 
 // ---------------------------------------------------------------- synthetic states
@@ -281,6 +324,9 @@ struct asse_mlp {
     float *y = nullptr, *dy = nullptr, *loss = nullptr;
     uint64_t steps = 0;
     int loss_kind = ASSE_LOSS_LOG_MSE;
+    // workspace of asse_report_learned, for rl_cap candidates
+    unsigned char *rl = nullptr;
+    uint64_t rl_cap = 0;
     uint64_t launches = 0;
     std::string err;
 };
@@ -440,6 +486,100 @@ int asse_estimate_learned(asse_pool *pool, asse_mlp *mlp, float max_log_n, uint1
     return ASSE_OK;
 }
 
+int asse_report_learned(asse_pool *pool, asse_mlp *m, float max_log_n, asse_superpoint *out, uint64_t cap,
+                        uint64_t *n_out, int where)
+{
+    if (!pool || !m || !n_out || !(max_log_n >= 0.0f) || (where != ASSE_HOST && where != ASSE_DEVICE))
+        return pool ? pool_fail(pool, ASSE_EINVAL, "NULL argument, negative max_log_n or unknown where") : ASSE_EINVAL;
+    FeatureView v;
+    if (int rc = pool_feature_view(pool, &v))
+        return rc;
+    if (m->stream != v.stream)
+        return pool_fail(pool, ASSE_EINVAL, "the model and the pool must use the same stream");
+    if (v.kp > 64)
+        return pool_fail(pool, ASSE_EINVAL, "features need k' <= 64");
+    // workspace, in 256-byte aligned parts of rl_cap records each: feature
+    // rows, candidate records, host addresses (then the model's outputs over
+    // them), reported records, and the count of reported records
+    auto part = [](uint64_t bytes) { return (bytes + 255) / 256 * 256; };
+    const uint64_t lcap = pool_list_cap(pool);
+    if (lcap > m->rl_cap) {
+        cudaFree(m->rl);  // waits for work that may still use the old workspace
+        m->rl = nullptr;
+        m->rl_cap = 0;
+        const uint64_t bytes = part(lcap * FEAT * sizeof(bf16)) + 2 * part(lcap * sizeof(asse_superpoint)) +
+                               part(lcap * sizeof(float)) + 256;
+        if (cudaMalloc((void **)&m->rl, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            m->rl = nullptr;
+            return pool_fail(pool, ASSE_ENOMEM, "workspace of the learned report");
+        }
+        m->rl_cap = lcap;
+    }
+    const uint64_t c = m->rl_cap;
+    uint16_t *x = reinterpret_cast<uint16_t *>(m->rl);
+    auto *cand = reinterpret_cast<asse_superpoint *>(m->rl + part(c * FEAT * sizeof(bf16)));
+    auto *yb = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(cand) + part(c * sizeof(asse_superpoint)));
+    auto *rep = reinterpret_cast<asse_superpoint *>(reinterpret_cast<unsigned char *>(yb) + part(c * sizeof(float)));
+    auto *n_rep_dev =
+        reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(rep) + part(c * sizeof(asse_superpoint)));
+    // the candidates of the last restore (synchronises; ECAPACITY passes on an overflowed restore)
+    uint64_t n = 0;
+    if (int rc = asse_candidates(pool, cand, c, &n, ASSE_DEVICE)) {
+        *n_out = n;
+        return rc;
+    }
+    *n_out = 0;
+    if (n == 0)
+        return ASSE_OK;
+    const uint64_t blocks = (n + 255) / 256, full = (uint64_t)v.sms * 4;
+    const unsigned grid = (unsigned)(blocks < full ? blocks : full);
+    uint32_t *aips = reinterpret_cast<uint32_t *>(yb);
+    cand_aips_kernel<<<grid, 256, 0, v.stream>>>(cand, n, aips);
+    *v.launches += 1;
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, std::string("candidate addresses: ") + cudaGetErrorString(e));
+    if (int rc = asse_candidate_features(pool, aips, n, x))
+        return rc;
+    std::string why;
+    if (int rc = launch_mlp_forward_tc(reinterpret_cast<const bf16 *>(x), n, m->w1p, m->w2p, m->params, yb, m->error,
+                                       v.stream, v.launches, &why))
+        return pool_fail(pool, rc == 1 ? ASSE_EINVAL : ASSE_ECUDA, why);
+    unsigned long long n_rep = 0;
+    int gave_up = 0;
+    cudaError_t e = cudaMemsetAsync(n_rep_dev, 0, sizeof(unsigned long long), v.stream);
+    if (e == cudaSuccess) {
+        learned_report_kernel<<<grid, 256, 0, v.stream>>>(cand, yb, n, max_log_n, (float)v.P.theta, rep, n_rep_dev);
+        *v.launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&n_rep, n_rep_dev, sizeof n_rep, cudaMemcpyDeviceToHost, v.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&gave_up, m->error, sizeof gave_up, cudaMemcpyDeviceToHost, v.stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(v.stream);
+    if (e != cudaSuccess)
+        return pool_fail(pool, ASSE_ECUDA, std::string("learned report: ") + cudaGetErrorString(e));
+    if (gave_up)
+        return pool_fail(pool, ASSE_ETIMEOUT, "the tensor-core MLP gave up waiting for its pipeline");
+    *n_out = n_rep;
+    const uint64_t k = n_rep < cap ? n_rep : cap;
+    if (k > 0) {
+        if (!out)
+            return pool_fail(pool, ASSE_EINVAL, "out is NULL");
+        e = cudaMemcpyAsync(out, rep, k * sizeof(asse_superpoint),
+                            where == ASSE_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, v.stream);
+        if (e == cudaSuccess && where != ASSE_DEVICE)
+            e = cudaStreamSynchronize(v.stream);
+        if (e != cudaSuccess)
+            return pool_fail(pool, ASSE_ECUDA, std::string("learned report copy: ") + cudaGetErrorString(e));
+    }
+    if (n_rep > cap)
+        return pool_fail(pool, ASSE_ECAPACITY, "output capacity smaller than the learned report");
+    return ASSE_OK;
+}
+
 int asse_synth_states(const asse_synth_cfg *cfg, uint64_t first, uint64_t n, uint16_t *x_dev, float *log_n_dev,
                       float *lc_dev, void *stream)
 {
@@ -550,7 +690,7 @@ void asse_mlp_destroy(asse_mlp *m)
     cudaStreamSynchronize(m->stream);
     for (void *p : {(void *)m->params, (void *)m->grads, (void *)m->m1, (void *)m->m2, (void *)m->w1b, (void *)m->w2b,
                     (void *)m->H1, (void *)m->H2, (void *)m->dZ2, (void *)m->dZ1, (void *)m->y, (void *)m->dy,
-                    (void *)m->loss, (void *)m->w1p, (void *)m->w2p, (void *)m->error})
+                    (void *)m->loss, (void *)m->w1p, (void *)m->w2p, (void *)m->error, (void *)m->rl})
         cudaFree(p);
     delete m;
 }

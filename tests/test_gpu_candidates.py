@@ -3,7 +3,11 @@
 their definition computed from the oracle's state (oracle/features.py); the
 synthetic candidate states the model is trained on are exactly what an oracle
 pool holds after ingesting the same host and background pairs; and a model
-trained on the GPU beats Eq. 4's relative error on held-out states."""
+trained on the GPU beats Eq. 4's relative error on held-out states; and the
+report decided by such a model on the device (asse_report_learned) is the
+one the oracle's features and FP64 network give."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -161,3 +165,85 @@ def test_candidate_model_beats_eq4(mods):
     assert rel_m.mean().item() < rel_e.mean().item(), (rel_m.mean().item(), rel_e.mean().item())
     mid = (lnt >= 9 * np.log(2)) & (lnt < 12 * np.log(2))
     assert rel_m[mid].mean().item() < rel_e[mid].mean().item(), (rel_m[mid].mean().item(), rel_e[mid].mean().item())
+
+
+@pytest.mark.parametrize("k,g,r,c,u,s,counter", [(10, 512, 4, 8, 0, 8, "at"), (6, 150, 4, 9, 2, 7, "hist")])
+def test_learned_report_matches_oracle(mods, k, g, r, c, u, s, counter):
+    """asse_report_learned against the oracle, slice by slice over a full 2k
+    cycle: the candidates are the oracle's restore (Algorithm 4), their
+    feature rows its state's (oracle/features.py), the model the FP64 network
+    with the GPU's parameters (oracle/mlp.py).  A candidate whose model output
+    lies clearly inside the training range (by more than its error scale) is
+    decided by exp(y) >= theta, one clearly outside keeps Eq. 4's decision;
+    only outputs within the error scale of ln(theta) or of the range's end
+    may go either way.  Estimates: exp(y) within the same scale for model
+    decisions, the restore's own record for Eq. 4 ones."""
+    asse, oracle, torch = mods
+    from oracle import features as ofeat
+    from oracle import mlp as omlp
+    theta = max(4, g // 3)
+    p = dict(k=k, theta=theta, g=g, r=r, c=c, u=u, s=s, **synth.method_keys(3 * k + g))
+    pool = asse.Pool(p, counter=counter, restore_cap=1 << 12)
+    orc = oracle.Oracle.from_params(p)
+    m = asse.MLP(seed=5)
+    base = m.params().astype(np.float64)
+    seen = {"learned_rep": 0, "learned_not": 0, "eq4": 0}
+    for t in range(2 * k + 2):
+        pairs = mixed_pairs(17, t, 4001, [theta // 2, theta, 2 * theta, 4 * theta])
+        pool.ingest(to_device(pairs))
+        orc.ingest(pairs)
+        pool.scan(k)
+        pool.restore()
+        res = orc.close_report(k, cap=pool.out_cap, limit_extra=0)
+        cand = pool.candidates()
+        assert sorted(int(a) for a in cand["aip"]) == [a for a, _e, _n in res["candidates"]]
+        if cand.size:
+            aips = np.sort(cand["aip"]).astype(np.uint32)
+            X = ofeat.pool_candidate_rows(orc, aips, k)
+            # outputs around ln(theta): a last layer of non-negative weights and
+            # no bias (no cancellation, so the error scale is about y itself),
+            # scaled so that the median output is ln(theta)
+            q = omlp.unpack(base)
+            q["w3"] = np.abs(q["w3"])
+            q["b3"] = np.zeros(1)
+            S = omlp.forward(omlp.pack(q), X)[0]
+            q["w3"] = q["w3"] * (np.log(theta) / max(float(np.median(S)), 1e-6))
+            m.set_params(omlp.pack(q).astype(np.float32))
+            params = m.params().astype(np.float64)
+            y = omlp.forward(params, X)[0]
+            tol = 2.0 ** -6 * omlp.error_scales(params, X, np.zeros(aips.size))[0]
+            max_log_n = float(np.quantile(y, 0.75)) if t % 2 else 40.0
+            got = pool.report_learned(m, max_log_n)
+            rec = {int(a): (float(e), int(f)) for a, e, f in zip(cand["aip"], cand["est"], cand["flags"])}
+            got_by = {int(a): (float(e), int(f)) for a, e, f in zip(got["aip"], got["est"], got["flags"])}
+            assert len(got_by) == got.size and set(got_by) <= set(rec)
+            for a, yi, ti in zip(aips.tolist(), y, tol):
+                if yi + ti <= max_log_n:                       # the model decides
+                    if abs(yi - np.log(theta)) <= ti:
+                        continue
+                    want = yi > np.log(theta)
+                    assert (a in got_by) == want, (t, a, yi, ti)
+                    seen["learned_rep" if want else "learned_not"] += 1
+                    if want:
+                        est, fl = got_by[a]
+                        assert fl & asse.SP_LEARNED and fl & asse.SP_REPORTED
+                        assert abs(np.log(est) - yi) <= ti + 1e-6, (a, est, yi, ti)
+                elif yi - ti > max_log_n:                      # Eq. 4 decides, as restored
+                    want = bool(rec[a][1] & asse.SP_REPORTED)
+                    assert (a in got_by) == want, (t, a)
+                    seen["eq4"] += 1
+                    if want:
+                        assert got_by[a] == rec[a]
+            if t == 2 * k + 1:                                 # an output too small for the report
+                n = ctypes.c_uint64(0)
+                rc = asse.lib().asse_report_learned(pool._h, m._h, ctypes.c_float(max_log_n), None, 0,
+                                                    ctypes.byref(n), asse.HOST)
+                assert n.value == got.size and rc == (asse.ECAPACITY if got.size else asse.OK)
+        pool.advance()
+        orc.advance()
+    with pytest.raises(asse.AsseError) as ei:          # refreshed since the scan
+        pool.report_learned(m, 40.0)
+    assert ei.value.status == asse.ESTATE
+    assert min(seen.values()) > 0, seen
+    m.close()
+    pool.close()
