@@ -483,6 +483,10 @@ def run_serve(args):
     waiting = list(range(n_streams))
     running = {}
     lat, pairs_done, deferred, max_open = [], 0, 0, 0
+    host_s = {"open": 0.0, "submit": 0.0, "poll": 0.0, "close": 0.0}
+    overflowed = 0
+    # the interval in which every admitted stream is open and none has closed yet
+    t_all_open, t_first_close, pairs_steady = None, None, 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     while waiting or running:
@@ -490,7 +494,9 @@ def run_serve(args):
             i = waiting[0]
             sp = streams[i][0]
             ctr = args.counter if args.counter != "auto" else auto_counter(sp["k"], sp["g"], sp["r"], sp["c"] + sp["u"])
+            th = time.perf_counter()
             sid = srv.open(sp, sp["k"], max_batch=16 << 20, counter=ctr)
+            host_s["open"] += time.perf_counter() - th
             if sid is None:
                 deferred += 1
                 break
@@ -499,22 +505,45 @@ def run_serve(args):
                 srv.attach_model(sid, model, 20 * float(np.log(2.0)))
             running[i] = [sid, 0, 0]          # sid, slices submitted, slices reported
         max_open = max(max_open, len(running))
+        if not waiting and t_all_open is None:
+            t_all_open = time.perf_counter()
         progressed = False
         for i in list(running):
             sid, sub, rep = running[i]
             if sub < slices_per_stream:
                 b = batch_for(i, sub)
-                if srv.submit(sid, b, close=True):
+                th = time.perf_counter()
+                ok = srv.submit(sid, b, close=True)
+                host_s["submit"] += time.perf_counter() - th
+                if ok:
                     running[i][1] += 1
                     pairs_done += b.shape[0]
                     progressed = True
-            r = srv.poll(sid)
+            th = time.perf_counter()
+            try:
+                r = srv.poll(sid)
+            except asse.AsseError as ex:
+                # a saturated small pool: more candidates than the restore
+                # capacity; the close is done and its report incomplete
+                if ex.status != asse.ECAPACITY:
+                    raise
+                r = "overflow"
+            host_s["poll"] += time.perf_counter() - th
             if r is not None:
-                lat.append(r[2])
+                if r == "overflow":
+                    overflowed += 1
+                else:
+                    lat.append(r[2])
+                if t_all_open is not None and t_first_close is None:
+                    pairs_steady += batch_for(i, running[i][2]).shape[0]
                 running[i][2] += 1
                 progressed = True
             if running[i][2] == slices_per_stream:
+                if t_first_close is None:
+                    t_first_close = time.perf_counter()
+                th = time.perf_counter()
                 srv.close(sid)
+                host_s["close"] += time.perf_counter() - th
                 del running[i]
         if not progressed:
             time.sleep(20e-6)
@@ -534,6 +563,13 @@ def run_serve(args):
                            "what": "device time from the start of a close to its report in host memory"},
             "pairs": pairs_done, "wall_s": wall, "closes": len(lat), "admission_deferrals": deferred,
             "max_streams_open": max_open,
+            "host_ms_in_calls": {k: 1e3 * v for k, v in host_s.items()},
+            "closes_over_restore_capacity": overflowed,
+            "steady": {"value": pairs_steady / (t_first_close - t_all_open)
+                       if t_all_open is not None and t_first_close is not None and t_first_close > t_all_open
+                       else None, "unit": "pkts/s",
+                       "what": "pairs of the closes reported while every admitted stream was open and none had "
+                               "closed yet, over that interval (no stream opening or closing in it)"},
             "learned_inference_in_close": bool(args.serve_learned)}
     print(json.dumps(line), flush=True)
 

@@ -175,6 +175,7 @@ class Server:
         if rc != OK:
             raise AsseError(rc, "asse_server_create failed")
         self.rcap = {}
+        self._bufs = {}
 
     def _err(self, rc):
         return AsseError(rc, lib().asse_server_last_error(self._h).decode())
@@ -208,6 +209,7 @@ class Server:
         if rc != OK:
             raise self._err(rc)
         self.rcap[sid.value] = (restore_cap or 4096)
+        self._bufs[sid.value] = np.empty(self.rcap[sid.value], dtype=SP_DTYPE)   # poll's output, reused
         return sid.value
 
     def submit(self, sid: int, pairs, close: bool) -> bool:
@@ -226,7 +228,7 @@ class Server:
     def poll(self, sid: int):
         """(report array, slice, latency ms) of the oldest finished close, or None."""
         cap = self.rcap[sid]
-        buf = np.zeros(cap, dtype=SP_DTYPE)
+        buf = self._bufs[sid]
         n, sl, ms = u64(0), u64(0), ctypes.c_float(0)
         rc = lib().asse_server_poll(self._h, sid, vp(buf.ctypes.data), cap, ctypes.byref(n), ctypes.byref(sl),
                                     ctypes.byref(ms))
@@ -234,7 +236,7 @@ class Server:
             return None
         if rc != OK:
             raise self._err(rc)
-        return buf[: n.value], int(sl.value), float(ms.value)
+        return buf[: n.value].copy(), int(sl.value), float(ms.value)
 
     def attach_model(self, sid: int, model, max_log_n: float):
         """Run learned per-ATV inference in every later close of stream sid."""

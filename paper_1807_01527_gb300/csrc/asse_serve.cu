@@ -26,8 +26,8 @@ namespace {
 struct Slot {
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
-    Status *status_host = nullptr;          // pinned
-    asse_superpoint *report_host = nullptr; // pinned, rcap records
+    Status *status_host = nullptr;          // pinned (in the stream's pinned block)
+    asse_superpoint *report_host = nullptr; // pinned, rcap records (same block)
     uint64_t slice = 0;
     // with a model attached: this close's learned estimates (device, r*E)
     // and its count of Eq. 2 fallbacks (device, and its pinned copy)
@@ -45,6 +45,10 @@ struct SStream {
     uint32_t *staging = nullptr;
     unsigned long long *n_dev = nullptr;
     cudaGraphExec_t ingest = nullptr;
+    // one pinned host block for the status and report copies of every slot:
+    // pinning host memory is slow and freeing it may wait for the device, so
+    // a stream does each once, when it opens and when it closes
+    unsigned char *pinned = nullptr;
     Slot ring[ASSE_SERVE_RING];
     uint32_t head = 0, count = 0;  // in-flight closes: ring[head] is the oldest
     int last_polled = -1;          // slot of the close the last successful poll returned
@@ -73,16 +77,14 @@ void release(SStream *st)
             cudaEventDestroy(sl.start);
         if (sl.done)
             cudaEventDestroy(sl.done);
-        if (sl.status_host)
-            cudaFreeHost(sl.status_host);
-        if (sl.report_host)
-            cudaFreeHost(sl.report_host);
         cudaFree(sl.est);
         cudaFree(sl.nfb_dev);
         if (sl.nfb_host)
             cudaFreeHost(sl.nfb_host);
         sl = Slot{};
     }
+    if (st->pinned)
+        cudaFreeHost(st->pinned);
     cudaFree(st->x);
     if (st->ingest)
         cudaGraphExecDestroy(st->ingest);
@@ -250,13 +252,16 @@ int asse_server_open(asse_server *srv, const asse_config *cfg, uint32_t kp, uint
     if (e == cudaSuccess)
         e = capture(st->s, &st->ingest, [&]() { return pool_enqueue_ingest(st->pool, st->staging, st->n_dev); },
                     &rc);
+    // per slot: the status, then the report, each part 256-byte aligned
+    const size_t status_part = (sizeof(Status) + 255) / 256 * 256;
+    const size_t slot_bytes = status_part + (st->rcap * sizeof(asse_superpoint) + 255) / 256 * 256;
+    if (e == cudaSuccess && rc == ASSE_OK)
+        e = cudaMallocHost((void **)&st->pinned, ASSE_SERVE_RING * slot_bytes);
     for (int i = 0; i < ASSE_SERVE_RING && e == cudaSuccess && rc == ASSE_OK; i++) {
         Slot &sl = st->ring[i];
-        e = cudaMallocHost((void **)&sl.status_host, sizeof(Status));
-        if (e == cudaSuccess)
-            e = cudaMallocHost((void **)&sl.report_host, st->rcap * sizeof(asse_superpoint));
-        if (e == cudaSuccess)
-            e = cudaEventCreate(&sl.start);
+        sl.status_host = reinterpret_cast<Status *>(st->pinned + i * slot_bytes);
+        sl.report_host = reinterpret_cast<asse_superpoint *>(st->pinned + i * slot_bytes + status_part);
+        e = cudaEventCreate(&sl.start);
         if (e == cudaSuccess)
             e = cudaEventCreate(&sl.done);
         if (e == cudaSuccess)
