@@ -510,7 +510,10 @@ def run_serve(args):
         progressed = False
         for i in list(running):
             sid, sub, rep = running[i]
-            if sub < slices_per_stream:
+            # submit only into a free report slot, poll only a stream with a
+            # close in flight: a call that can only answer "again" still
+            # costs the loop its host time
+            if sub < slices_per_stream and sub - rep < asse.SERVE_RING:
                 b = batch_for(i, sub)
                 th = time.perf_counter()
                 ok = srv.submit(sid, b, close=True)
@@ -519,6 +522,8 @@ def run_serve(args):
                     running[i][1] += 1
                     pairs_done += b.shape[0]
                     progressed = True
+            if running[i][1] == running[i][2]:
+                continue
             th = time.perf_counter()
             try:
                 r = srv.poll(sid)

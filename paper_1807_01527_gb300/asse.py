@@ -21,6 +21,7 @@ COUNTER_AT, COUNTER_ACE, COUNTER_AT_ALIGNED, COUNTER_AT_HIST = 0, 1, 2, 3
 COUNTERS = {"at": COUNTER_AT, "ace": COUNTER_ACE, "aligned": COUNTER_AT_ALIGNED, "hist": COUNTER_AT_HIST}
 KEY_TABLE = {"auto": 0, "on": 1, "off": 2}
 SP_SATURATED, SP_REPORTED, SP_LEARNED = 1, 2, 4
+SERVE_RING = 4   # ASSE_SERVE_RING of include/asse_serve.h: closes a stream may have in flight
 
 u32, u64, i32, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
 

@@ -76,6 +76,7 @@ def test_null_arguments(lib):
     assert lib.asse_strerror(asse.ECAPACITY) == b"ASSE_ECAPACITY"
     assert lib.asse_strerror(asse.EAGAIN) == b"ASSE_EAGAIN"
     assert lib.asse_strerror(asse.ETIMEOUT) == b"ASSE_ETIMEOUT"
+    assert lib.asse_report_learned(None, None, 1.0, None, 0, None, asse.HOST) == asse.EINVAL
     # the wait bound is checked before any CUDA call
     assert lib.asse_probe_bounded_wait(None, 0, 0, None) == asse.EINVAL
     assert lib.asse_probe_bounded_wait(None, (1 << 36) + 1, 0, None) == asse.EINVAL
