@@ -529,3 +529,31 @@ def test_long_report_beyond_the_early_copy(mods):
         if t == 1:
             assert len(res["report"]) > 4096, len(res["report"])
         orc.advance()
+
+
+@pytest.mark.parametrize("counter,key_table", [("at", "off"), ("at", "on"), ("hist", "on"), ("ace", "off")])
+def test_replayed_permuted_and_truncated_batches(mods, counter, key_table):
+    """SetAT is idempotent within a slice (Sec. 4.4): a batch cut short
+    leaves the pool as the oracle fed the same prefix, and that prefix
+    ingested again, then again in another order, changes nothing: the state,
+    the counts (for slice-count pools, the counts the ingest keeps) and the
+    report stay the oracle's, slice after slice over a full 2k cycle."""
+    asse, oracle, torch = mods
+    k, g, r, c, u, s, theta = 6, 150, 4, 9, 2, 7, 50
+    p = _params(k, g, r, c, u, s, theta, seed=11)
+    pool = asse.Pool(p, counter=counter, key_table=key_table)
+    orc = oracle.Oracle.from_params(p, mode=1 if counter == "ace" else 0)
+    rng = np.random.default_rng(4)
+    for t in range(2 * k + 3):
+        pairs = mixed_pairs(21, t, 20001, [theta // 2, theta, 3 * theta])
+        cut = int(rng.integers(1, pairs.shape[0]))
+        pool.ingest(to_device(pairs[:cut]))
+        orc.ingest(pairs[:cut])
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"truncated batch, t={t}")
+        pool.ingest(to_device(pairs[:cut]))
+        pool.ingest(to_device(np.ascontiguousarray(pairs[:cut][rng.permutation(cut)])))
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"replayed batch, t={t}")
+        check_close(pool, orc, k)
+        orc.advance()
+        np.testing.assert_array_equal(state(pool), orc.at(), err_msg=f"after refresh t={t}")
+    pool.close()

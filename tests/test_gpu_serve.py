@@ -203,3 +203,32 @@ def test_learned_inference_in_close_graphs(mods, counter):
     assert 0 < min(want_nfb) and max(want_nfb) < rows      # both the model and the fallback were used
     srv.close(sid)
     srv.destroy()
+
+
+def test_close_with_closes_in_flight(mods):
+    """A stream closed while closes of it are still queued (never polled)
+    ends cleanly: its memory returns to the budget, and a stream opened in
+    its place, fed the same batches, reports exactly what the oracle does."""
+    asse, torch = mods
+    p, k, slices = _streams()[1]
+    size = asse.Server.stream_bytes(p, 40000)
+    srv = asse.Server(size)                            # room for one stream only
+    sid = srv.open(p, k, max_batch=40000)
+    for batches in slices[:asse.SERVE_RING]:
+        for j, b in enumerate(batches):
+            assert srv.submit(sid, b, close=(j == len(batches) - 1))
+    assert srv.open(p, k, max_batch=40000) is None     # the budget is taken
+    srv.close(sid)                                     # four closes still queued
+    assert srv.bytes_in_use() == 0
+    sid = srv.open(p, k, max_batch=40000)
+    assert sid is not None
+    for t, (batches, rows) in enumerate(zip(slices, _oracle_reports(p, k, slices))):
+        for j, b in enumerate(batches):
+            assert srv.submit(sid, b, close=(j == len(batches) - 1))
+        res = None
+        while res is None:
+            res = srv.poll(sid)
+        compare_lists(res[0], rows, p["theta"], "slice %d" % t)
+    srv.close(sid)
+    assert srv.bytes_in_use() == 0
+    srv.destroy()
